@@ -1,0 +1,253 @@
+/*
+ * sil.h -- C ABI of the GB300 sea-ice auto-labeler (libsil.so).
+ *
+ * The library labels Sentinel-2 true-colour imagery per pixel as thick /
+ * snow-covered ice, young / thin ice, open water or masked, after a thin
+ * cloud and shadow filter, and reduces the labels to per-chip and per-request
+ * class counts, in one fused pass on the GPU.  It follows
+ *   "A Parallel Workflow for Polar Sea-Ice Classification using Auto-labeling
+ *    of Sentinel-2 Imagery" (arXiv 2403.13135):
+ *   - Sec. III-A: inputs are bands 2/3/4 (blue, green, red) at 10 m, cut into
+ *     256 x 256 chips;
+ *   - Sec. III-B "Filtering Out the Thin Clouds and Shadows": the filter is
+ *     built from HSV conversion, noise filtering, Otsu thresholding, min-max
+ *     normalisation, truncated / binary thresholding, absolute difference and
+ *     bit-wise operations (composition "F1", described at sil_params);
+ *   - Sec. III-B "Auto-labeling Method": inclusive HSV ranges per class,
+ *     thick (0,0,205)-(185,255,255), thin (0,0,31)-(185,255,204),
+ *     water (0,0,0)-(185,255,30), one mask per class, masks merged;
+ *   - Sec. III-B "PySpark Map-Reduce": map = label an image, reduce =
+ *     collect; here the reduce is a class count per chip and per request.
+ *
+ * Label codes: 0 thick ice, 1 thin ice, 2 open water, 3 masked.
+ *
+ * Conventions for every call:
+ *   - Image, label and count buffers are owned by the caller.  Unless a
+ *     function says otherwise they are DEVICE pointers of the current device.
+ *   - Calls are asynchronous on the given stream (NULL = legacy default
+ *     stream); a returned SIL_OK means the work was enqueued.
+ *   - Arguments are validated on the host before anything is launched; a bad
+ *     argument returns SIL_EINVAL and launches nothing.  CUDA errors return
+ *     SIL_ECUDA.  sil_last_error() gives a message for the calling thread.
+ *   - All arithmetic is integer; results are bit-exact and do not depend on
+ *     launch configuration, stream or batching.
+ */
+#ifndef SIL_H_
+#define SIL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIL_ABI_VERSION 1
+
+/* cudaStream_t is `struct CUstream_st*`; declared here so this header does
+ * not need the CUDA headers. */
+typedef struct CUstream_st* sil_stream;
+
+typedef enum sil_status {
+  SIL_OK = 0,
+  SIL_EINVAL = 1,    /* invalid argument (nothing launched) */
+  SIL_ENOMEM = 2,    /* device or host allocation failed */
+  SIL_ECUDA = 3,     /* a CUDA call failed */
+  SIL_ETIMEOUT = 4,  /* a bounded wait ran out */
+  SIL_EBUSY = 5,     /* no free slot / memory right now; retry later */
+  SIL_ECANCELED = 6  /* request cancelled or server shut down */
+} sil_status;
+
+typedef enum sil_dtype {
+  SIL_U8 = 0,  /* 3 x uint8 per pixel (8-bit true colour) */
+  SIL_U16 = 1  /* 3 x uint16 per pixel (S2 reflectance, little-endian) */
+} sil_dtype;
+
+/* Parameters.  Defaults (sil_params_default) are the paper's class ranges
+ * (Sec. III-B) and the filter reading F1:
+ *   V = max(R,G,B); Vf = 3x3 median of V inside the chip (replicated
+ *   border) [noise filtering]; per chip over non-nodata pixels: lo/hi =
+ *   min/max of Vf, Otsu threshold t [Otsu]; stretch Vf to [0,255] when
+ *   hi - lo >= mm_min_range and both Otsu classes hold >= N/mm_min_frac_den
+ *   pixels [min-max normalisation]; V' = min(stretched, v_trunc)
+ *   [truncated threshold]; class masks by inclusive ranges on (H, S, V')
+ *   merged with precedence thick > thin > water, no match -> masked
+ *   [binary thresholds, bit-wise ops]; a pixel whose |V' - Vf| > max_shift
+ *   is masked [absolute difference].
+ * H is hue in degrees / 2 (0..179), S and V are 0..255, all rounded half up.
+ * filter = 0 skips every filter step (classes on raw H, S, V).
+ * uint16 input is brought to 8 bit by round(v * 255 / u16_scale) clamped to
+ * 255; a pixel with all three raw channels 0 is S2 nodata and is masked. */
+typedef struct sil_params {
+  uint8_t lo[3][3];        /* [thick, thin, water][H, S, V], inclusive */
+  uint8_t hi[3][3];        /* lo <= hi required */
+  int32_t filter;          /* 0 or 1 (default 1) */
+  int32_t chip;            /* statistics / count chip side, 4..512 (256) */
+  int32_t median;          /* 0 or 1 (1) */
+  int32_t mm_min_range;    /* 1..255 (64) */
+  int32_t mm_min_frac_den; /* 1..65536 (16) */
+  int32_t v_trunc;         /* 0..255 (255 = no truncation) */
+  int32_t max_shift;       /* 0..255 (255 = never masks) */
+  int32_t bgr;             /* 0: bytes are R,G,B; 1: B,G,R (OpenCV order) */
+  int32_t u16_scale;       /* 1..65535 (10000) */
+} sil_params;
+
+/* Fill *p with the defaults.  Returns SIL_EINVAL if p is NULL. */
+sil_status sil_params_default(sil_params* p);
+
+/* SIL_OK if every field is in range, else SIL_EINVAL (message in
+ * sil_last_error). */
+sil_status sil_params_validate(const sil_params* p);
+
+/* Static text for a status code; never NULL. */
+const char* sil_status_string(sil_status s);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* sil_last_error(void);
+
+/* Library ABI version (SIL_ABI_VERSION). */
+int sil_version(void);
+
+/* Label one request (a tile or a scene), fused single pass on the GPU.
+ *   img          device, H x W pixels, 3 interleaved channels of dt, rows
+ *                pitch_bytes apart (pitch_bytes >= 3 W sizeof(dt)); uint16
+ *                images need 2-byte aligned img and pitch.  No alignment is
+ *                required otherwise.
+ *   H, W         >= 1, H * W < 2^40.
+ *   p            host pointer; NULL = defaults.
+ *   labels       device, H x W uint8 codes with label_pitch >= W bytes per
+ *                row; NULL = do not write labels (counts only).
+ *   counts       device uint64[4], OVERWRITTEN with the request's totals
+ *                (thick, thin, water, masked); required.
+ *   chip_counts  device uint32[ceil(H/chip)][ceil(W/chip)][4] row-major, one
+ *                entry per chip of the grid anchored at (0,0); may be NULL.
+ * Statistics (Otsu, min/max) are taken per chip (Sec. III-A / III-C: the
+ * paper filters 256 x 256 chips).  Nothing is allocated; the call only
+ * enqueues a memset of counts and one kernel. */
+sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
+                     sil_dtype dt, const sil_params* p, uint8_t* labels,
+                     int64_t label_pitch, uint64_t* counts,
+                     uint32_t* chip_counts, sil_stream stream);
+
+/* Same as sil_label but the image, labels and counts are HOST buffers; the
+ * library stages them through its own device buffers (pitched copy in,
+ * labels and counts back) on `stream` and returns when the results are in
+ * host memory.  Pinned host memory gives the fastest copies.  labels and
+ * chip_counts may be NULL.  Device buffers are cached per host thread and
+ * reused across calls. */
+sil_status sil_label_host(const void* img, int64_t H, int64_t W,
+                          int64_t pitch_bytes, sil_dtype dt, const sil_params* p,
+                          uint8_t* labels, int64_t label_pitch,
+                          uint64_t* counts, uint32_t* chip_counts,
+                          sil_stream stream);
+
+/* ---------------------------------------------------------------------
+ * Batched labeling (one persistent launch over a work queue of uneven
+ * tiles, captured in a CUDA graph).  Mirrors the paper's PySpark map over
+ * a collection of images (Sec. III-B "PySpark Map-Reduce"): each tile is
+ * labelled independently and reduced to its own counts.
+ * ------------------------------------------------------------------- */
+typedef struct sil_tile {
+  const void* img;       /* device */
+  int64_t H, W, pitch_bytes;
+  uint8_t* labels;       /* device, may be NULL */
+  int64_t label_pitch;
+  uint64_t* counts;      /* device uint64[4], overwritten */
+  uint32_t* chip_counts; /* device, may be NULL */
+} sil_tile;
+
+typedef struct sil_ctx sil_ctx;
+
+/* Create a context on `device` (the current device is restored on return).
+ * The context owns the batch work queue, tile descriptors, graph cache and
+ * autotune results; it is not thread-safe (one host thread at a time). */
+sil_status sil_ctx_create(sil_ctx** ctx, int device);
+void sil_ctx_destroy(sil_ctx* ctx);
+
+/* Label n tiles (host array of descriptors) with one persistent kernel.
+ * All tiles share dt and p.  The launch is recorded once into a CUDA graph
+ * per (n, dt, params, tile list) and replayed when the same batch comes
+ * again.  Returns after enqueueing on `stream`. */
+sil_status sil_label_batch(const sil_tile* tiles, int32_t n, sil_dtype dt,
+                           const sil_params* p, sil_ctx* ctx, sil_stream stream);
+
+/* Pick the persistent schedule (CTAs per SM, chip-order policy) for the
+ * given batch by timing the candidates on `stream`; the result is cached in
+ * ctx and used by later sil_label_batch calls with the same dt.  Blocks
+ * until the timing is done.  best_ctas_per_sm may be NULL. */
+sil_status sil_autotune(const sil_tile* tiles, int32_t n, sil_dtype dt,
+                        const sil_params* p, sil_ctx* ctx, sil_stream stream,
+                        int32_t* best_ctas_per_sm);
+
+/* ---------------------------------------------------------------------
+ * Served labeling: a continuous-batching request loop.  Requests arrive at
+ * any time with HOST images (pinned memory recommended); they are admitted
+ * when device memory and a slot are free, copied in on an ingest stream,
+ * labelled by persistent launches that take every admitted request at once,
+ * and completed with results copied back to the caller's host buffers.
+ * ------------------------------------------------------------------- */
+typedef struct sil_server sil_server;
+
+typedef struct sil_server_config {
+  int32_t device;             /* CUDA device */
+  int32_t max_inflight;       /* request slots (default 64) */
+  int64_t device_mem_budget;  /* bytes of device memory for request buffers;
+                                 0 = 50% of free memory at create */
+  int32_t max_batch;          /* requests per launch (default 32) */
+  int32_t want_labels;        /* 1: copy labels back (default 1) */
+} sil_server_config;
+
+typedef struct sil_request_result {
+  int64_t id;
+  sil_status status;
+  uint64_t counts[4];
+  double t_submit_ms, t_admit_ms, t_done_ms; /* host monotonic clock */
+} sil_request_result;
+
+sil_status sil_server_config_default(sil_server_config* cfg);
+sil_status sil_server_create(sil_server** srv, const sil_server_config* cfg,
+                             sil_dtype dt, const sil_params* p);
+/* Submit one request.  img and labels are HOST buffers that must stay valid
+ * until the request completes (labels may be NULL).  chip_counts (host, may
+ * be NULL) receives the per-chip counts.  *id receives the request id.
+ * Returns SIL_EBUSY if the request can never fit the memory budget. */
+sil_status sil_server_submit(sil_server* srv, const void* img, int64_t H,
+                             int64_t W, int64_t pitch_bytes, uint8_t* labels,
+                             int64_t label_pitch, uint32_t* chip_counts,
+                             int64_t* id);
+/* Wait up to timeout_ms (-1 = no limit) for request `id` to complete.
+ * SIL_ETIMEOUT if it did not complete in time. */
+sil_status sil_server_wait(sil_server* srv, int64_t id, int64_t timeout_ms,
+                           sil_request_result* out);
+/* Non-blocking: SIL_OK and *out filled if done, SIL_EBUSY if not yet. */
+sil_status sil_server_poll(sil_server* srv, int64_t id, sil_request_result* out);
+/* Cancel a request that has not been admitted yet (SIL_EBUSY if it is
+ * already running). */
+sil_status sil_server_cancel(sil_server* srv, int64_t id);
+/* Stop accepting work, cancel pending requests, wait for running ones and
+ * free everything. */
+void sil_server_destroy(sil_server* srv);
+
+/* ---------------------------------------------------------------------
+ * Confusion counts of a label map against a reference map (Sec. IV-A:
+ * accuracy, precision, recall, F1 and the confusion matrix are computed from
+ * these counts).  conf: device uint64[4][4] indexed [pred][ref], overwritten;
+ * chip_conf: device uint32[gy][gx][4][4] or NULL.  Labels must be 0..3.
+ * ------------------------------------------------------------------- */
+sil_status sil_confusion(const uint8_t* pred, int64_t pred_pitch,
+                         const uint8_t* ref, int64_t ref_pitch, int64_t H,
+                         int64_t W, int32_t chip, uint64_t* conf,
+                         uint32_t* chip_conf, sil_stream stream);
+
+/* Render labels as the paper's colour masks (Sec. III-B: each class mask
+ * gets its own colour; Fig. 3 legend: thick ice red, thin ice blue, open
+ * water green; masked pixels black).  rgb: device, H x W x 3 uint8 with
+ * rgb_pitch bytes per row. */
+sil_status sil_render(const uint8_t* labels, int64_t label_pitch, int64_t H,
+                      int64_t W, uint8_t* rgb, int64_t rgb_pitch,
+                      sil_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIL_H_ */

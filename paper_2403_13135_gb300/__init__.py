@@ -1,0 +1,296 @@
+"""Python binding of libsil, the GB300 sea-ice auto-labeler.
+
+Argument marshalling only: every step of the labelling runs in the CUDA
+kernels of ``libsil.so`` behind the C ABI declared in ``include/sil.h``.
+PyTorch supplies device memory and streams.  Importing this package loads
+``libsil.so`` and raises ``ImportError`` if it is missing -- there is no CPU
+fallback.
+
+Same names as the C ABI (``sil_label``, ``sil_label_batch``, ...) taking
+integer pointers; plus helpers (``label``, ``label_host``, ``label_batch``,
+``Server``) that take torch tensors / numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsil.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsil.so not built ({LIB_PATH}); run python paper_2403_13135_gb300/build.py")
+_lib = ctypes.CDLL(LIB_PATH)
+
+SIL_OK, SIL_EINVAL, SIL_ENOMEM, SIL_ECUDA, SIL_ETIMEOUT, SIL_EBUSY, SIL_ECANCELED = range(7)
+SIL_U8, SIL_U16 = 0, 1
+THICK, THIN, WATER, MASKED = 0, 1, 2, 3
+
+
+class SilError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.sil_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+class sil_params(ctypes.Structure):
+    _fields_ = [
+        ("lo", (ctypes.c_uint8 * 3) * 3),
+        ("hi", (ctypes.c_uint8 * 3) * 3),
+        ("filter", ctypes.c_int32),
+        ("chip", ctypes.c_int32),
+        ("median", ctypes.c_int32),
+        ("mm_min_range", ctypes.c_int32),
+        ("mm_min_frac_den", ctypes.c_int32),
+        ("v_trunc", ctypes.c_int32),
+        ("max_shift", ctypes.c_int32),
+        ("bgr", ctypes.c_int32),
+        ("u16_scale", ctypes.c_int32),
+    ]
+
+
+class sil_tile(ctypes.Structure):
+    _fields_ = [
+        ("img", ctypes.c_void_p),
+        ("H", ctypes.c_int64), ("W", ctypes.c_int64), ("pitch_bytes", ctypes.c_int64),
+        ("labels", ctypes.c_void_p), ("label_pitch", ctypes.c_int64),
+        ("counts", ctypes.c_void_p), ("chip_counts", ctypes.c_void_p),
+    ]
+
+
+class sil_server_config(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+        ("device_mem_budget", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+        ("want_labels", ctypes.c_int32),
+    ]
+
+
+class sil_request_result(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_int64), ("status", ctypes.c_int32),
+        ("counts", ctypes.c_uint64 * 4),
+        ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+        ("t_done_ms", ctypes.c_double),
+    ]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_SIGS = {
+    "sil_params_default": ([ctypes.POINTER(sil_params)], _I32),
+    "sil_params_validate": ([ctypes.POINTER(sil_params)], _I32),
+    "sil_status_string": ([_I32], ctypes.c_char_p),
+    "sil_last_error": ([], ctypes.c_char_p),
+    "sil_version": ([], ctypes.c_int),
+    "sil_label": ([_P, _I64, _I64, _I64, _I32, ctypes.POINTER(sil_params), _P, _I64, _P, _P, _P], _I32),
+    "sil_label_host": ([_P, _I64, _I64, _I64, _I32, ctypes.POINTER(sil_params), _P, _I64, _P, _P, _P], _I32),
+    "sil_ctx_create": ([ctypes.POINTER(_P), _I32], _I32),
+    "sil_ctx_destroy": ([_P], None),
+    "sil_label_batch": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P, _P], _I32),
+    "sil_autotune": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P, _P,
+                      ctypes.POINTER(_I32)], _I32),
+    "sil_server_config_default": ([ctypes.POINTER(sil_server_config)], _I32),
+    "sil_server_create": ([ctypes.POINTER(_P), ctypes.POINTER(sil_server_config), _I32,
+                           ctypes.POINTER(sil_params)], _I32),
+    "sil_server_submit": ([_P, _P, _I64, _I64, _I64, _P, _I64, _P, ctypes.POINTER(_I64)], _I32),
+    "sil_server_wait": ([_P, _I64, _I64, ctypes.POINTER(sil_request_result)], _I32),
+    "sil_server_poll": ([_P, _I64, ctypes.POINTER(sil_request_result)], _I32),
+    "sil_server_cancel": ([_P, _I64], _I32),
+    "sil_server_destroy": ([_P], None),
+    "sil_confusion": ([_P, _I64, _P, _I64, _I64, _I64, _I32, _P, _P, _P], _I32),
+    "sil_render": ([_P, _I64, _I64, _I64, _P, _I64, _P], _I32),
+}
+EXPORTED = tuple(_SIGS)
+
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name, None)
+    if _f is None:
+        continue
+    _f.argtypes = _args
+    _f.restype = _res
+    globals()[_name] = _f
+
+
+def check(status: int) -> None:
+    if status != SIL_OK:
+        raise SilError(status, (_lib.sil_last_error() or b"").decode())
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+def params(**overrides) -> sil_params:
+    """Default parameters (paper class ranges, filter F1) with overrides;
+    ``lo`` / ``hi`` take 3 x 3 nested lists."""
+    p = sil_params()
+    check(_lib.sil_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if k.startswith("_"):
+            continue
+        if k in ("lo", "hi"):
+            arr = getattr(p, k)
+            for a in range(3):
+                for b in range(3):
+                    arr[a][b] = int(v[a][b])
+        else:
+            setattr(p, k, int(v))
+    return p
+
+
+def _as_params(p) -> sil_params:
+    if p is None:
+        return params()
+    if isinstance(p, sil_params):
+        return p
+    return params(**dict(p))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _img_geometry(img):
+    """(H, W, pitch_bytes, dtype) of an H x W x 3 uint8/uint16 tensor whose
+    rows may be padded (stride(0) >= 3 W)."""
+    import torch
+    assert img.dim() == 3 and img.shape[2] == 3, "image must be H x W x 3"
+    assert img.stride(2) == 1 and img.stride(1) == 3, "pixels must be interleaved"
+    if img.dtype == torch.uint8:
+        dt, es = SIL_U8, 1
+    elif img.dtype in (torch.uint16, torch.int16):
+        dt, es = SIL_U16, 2
+    else:
+        raise TypeError(f"unsupported dtype {img.dtype}")
+    return img.shape[0], img.shape[1], img.stride(0) * es, dt
+
+
+def label(img, p=None, *, labels=True, chip_counts=False, out_labels=None,
+          out_counts=None, out_chip_counts=None, stream=None):
+    """Label one device image (torch CUDA tensor H x W x 3, uint8 or uint16).
+
+    Returns (labels uint8 H x W or None, counts uint64[4] as int64 tensor,
+    chip_counts int32 [gy, gx, 4] or None).  Asynchronous on ``stream``."""
+    import torch
+    H, W, pitch, dt = _img_geometry(img)
+    pp = _as_params(p)
+    C = pp.chip
+    gy, gx = -(-H // C), -(-W // C)
+    dev = img.device
+    lab = None
+    if labels:
+        lab = out_labels if out_labels is not None else torch.empty((H, W), dtype=torch.uint8, device=dev)
+    cnt = out_counts if out_counts is not None else torch.empty(4, dtype=torch.int64, device=dev)
+    cc = None
+    if chip_counts:
+        cc = out_chip_counts if out_chip_counts is not None else torch.empty((gy, gx, 4), dtype=torch.int32, device=dev)
+    check(_lib.sil_label(img.data_ptr(), H, W, pitch, dt, ctypes.byref(pp),
+                         lab.data_ptr() if lab is not None else None,
+                         lab.stride(0) if lab is not None else W,
+                         cnt.data_ptr(), cc.data_ptr() if cc is not None else None,
+                         _stream_handle(stream)))
+    return lab, cnt, cc
+
+
+def label_host(img: np.ndarray, p=None, *, labels=True, chip_counts=False, stream=None):
+    """Label a HOST image (numpy H x W x 3 uint8/uint16, ideally in pinned
+    memory); returns numpy (labels, counts uint64[4], chip_counts)."""
+    assert img.ndim == 3 and img.shape[2] == 3
+    H, W = img.shape[:2]
+    dt = SIL_U8 if img.dtype == np.uint8 else SIL_U16
+    pp = _as_params(p)
+    C = pp.chip
+    gy, gx = -(-H // C), -(-W // C)
+    lab = np.empty((H, W), np.uint8) if labels else None
+    cnt = np.zeros(4, np.uint64)
+    cc = np.zeros((gy, gx, 4), np.uint32) if chip_counts else None
+    check(_lib.sil_label_host(img.ctypes.data, H, W, img.strides[0], dt, ctypes.byref(pp),
+                              lab.ctypes.data if lab is not None else None, W,
+                              cnt.ctypes.data, cc.ctypes.data if cc is not None else None,
+                              _stream_handle(stream)))
+    return lab, cnt, cc
+
+
+class Context:
+    """Owns a sil_ctx (batch work queue, graph cache, autotune results)."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.handle = ctypes.c_void_p()
+        check(_lib.sil_ctx_create(ctypes.byref(self.handle), int(device)))
+
+    def close(self):
+        if self.handle:
+            _lib.sil_ctx_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_tiles(imgs, labels=None, counts=None, chip_counts=None):
+    """ctypes array of sil_tile for lists of device tensors."""
+    n = len(imgs)
+    arr = (sil_tile * n)()
+    for i, im in enumerate(imgs):
+        H, W, pitch, _ = _img_geometry(im)
+        t = arr[i]
+        t.img = im.data_ptr()
+        t.H, t.W, t.pitch_bytes = H, W, pitch
+        lab = labels[i] if labels is not None else None
+        t.labels = lab.data_ptr() if lab is not None else None
+        t.label_pitch = lab.stride(0) if lab is not None else W
+        t.counts = counts[i].data_ptr()
+        cc = chip_counts[i] if chip_counts is not None else None
+        t.chip_counts = cc.data_ptr() if cc is not None else None
+    return arr
+
+
+def label_batch(ctx: Context, tiles, n: int, dt: int = SIL_U8, p=None, stream=None):
+    pp = _as_params(p)
+    check(_lib.sil_label_batch(tiles, int(n), int(dt), ctypes.byref(pp), ctx.handle,
+                               _stream_handle(stream)))
+
+
+def autotune(ctx: Context, tiles, n: int, dt: int = SIL_U8, p=None, stream=None) -> int:
+    pp = _as_params(p)
+    best = _I32(0)
+    check(_lib.sil_autotune(tiles, int(n), int(dt), ctypes.byref(pp), ctx.handle,
+                            _stream_handle(stream), ctypes.byref(best)))
+    return best.value
+
+
+def confusion(pred, ref, chip: int = 256, chip_conf: bool = False, stream=None):
+    """Confusion counts [pred][ref] of two device label maps (uint8 H x W)."""
+    import torch
+    H, W = pred.shape
+    conf = torch.empty((4, 4), dtype=torch.int64, device=pred.device)
+    cc = None
+    if chip_conf:
+        cc = torch.empty((-(-H // chip), -(-W // chip), 4, 4), dtype=torch.int32, device=pred.device)
+    check(_lib.sil_confusion(pred.data_ptr(), pred.stride(0), ref.data_ptr(), ref.stride(0), H, W,
+                             int(chip), conf.data_ptr(), cc.data_ptr() if cc is not None else None,
+                             _stream_handle(stream)))
+    return conf, cc
+
+
+def render(labels, stream=None):
+    """Colour image (H x W x 3 uint8, device) of a label map: thick red,
+    thin blue, water green, masked black."""
+    import torch
+    H, W = labels.shape
+    rgb = torch.empty((H, W, 3), dtype=torch.uint8, device=labels.device)
+    check(_lib.sil_render(labels.data_ptr(), labels.stride(0), H, W, rgb.data_ptr(), 3 * W,
+                          _stream_handle(stream)))
+    return rgb

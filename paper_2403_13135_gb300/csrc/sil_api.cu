@@ -1,0 +1,456 @@
+// sil_api.cu -- C ABI entry points of libsil: parameters, single-request
+// labelling (device and host buffers), confusion counts and colour render.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "sil.h"
+#include "sil_chip.cuh"
+#include "sil_common.h"
+#include "sil_generic.cuh"
+
+namespace sil {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+sil_status derive_params(const sil_params* p, DevParams* dp) {
+  sil_params def;
+  if (!p) {
+    sil_params_default(&def);
+    p = &def;
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c)
+      if (p->lo[k][c] > p->hi[k][c]) {
+        set_error("params: lo[%d][%d]=%d > hi[%d][%d]=%d", k, c, p->lo[k][c], k, c, p->hi[k][c]);
+        return SIL_EINVAL;
+      }
+#define SIL_RANGE(f, a, b)                                                \
+  if (p->f < (a) || p->f > (b)) {                                         \
+    set_error("params: %s=%d outside [%d, %d]", #f, int(p->f), int(a), int(b)); \
+    return SIL_EINVAL;                                                    \
+  }
+  SIL_RANGE(filter, 0, 1)
+  SIL_RANGE(chip, 4, 512)
+  SIL_RANGE(median, 0, 1)
+  SIL_RANGE(mm_min_range, 1, 255)
+  SIL_RANGE(mm_min_frac_den, 1, 65536)
+  SIL_RANGE(v_trunc, 0, 255)
+  SIL_RANGE(max_shift, 0, 255)
+  SIL_RANGE(bgr, 0, 1)
+  SIL_RANGE(u16_scale, 1, 65535)
+#undef SIL_RANGE
+  memset(dp, 0, sizeof(*dp));
+  memcpy(dp->lo, p->lo, sizeof(dp->lo));
+  memcpy(dp->hi, p->hi, sizeof(dp->hi));
+  dp->filter = p->filter;
+  dp->median = p->median;
+  dp->mm_min_range = p->mm_min_range;
+  dp->frac_den = p->mm_min_frac_den;
+  dp->v_trunc = p->v_trunc;
+  dp->max_shift = p->max_shift;
+  dp->bgr = p->bgr;
+  dp->need_hs = 0;
+  for (int k = 0; k < 3; ++k)
+    if (p->lo[k][0] > 0 || p->hi[k][0] < 179 || p->lo[k][1] > 0 || p->hi[k][1] < 255)
+      dp->need_hs = 1;
+  const uint64_t s = uint64_t(p->u16_scale);
+  dp->u16_half = uint32_t(s / 2);
+  dp->u16_mul = ((uint64_t(1) << 40) + s - 1) / s;
+  // The quotient by multiplication must be exact on every input it meets.
+  static thread_local int checked_scale = -1;
+  if (checked_scale != p->u16_scale) {
+    for (uint64_t x = 0; x < 65536; ++x) {
+      const uint64_t n = x * 255 + dp->u16_half;
+      if (((n * dp->u16_mul) >> 40) != n / s) {
+        set_error("params: no exact reciprocal for u16_scale=%d", p->u16_scale);
+        return SIL_EINVAL;
+      }
+    }
+    checked_scale = p->u16_scale;
+  }
+  return SIL_OK;
+}
+
+static sil_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return SIL_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels.
+// ---------------------------------------------------------------------------
+template <int DT, bool HS>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_label(Req r, DevParams dp, int chip) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ uint8_t lut[256];
+  ChipSmem& sm = *reinterpret_cast<ChipSmem*>(smem_raw);
+  ChipFlags* fl = (HS || DT == SIL_U16)
+                      ? reinterpret_cast<ChipFlags*>(smem_raw + sizeof(ChipSmem))
+                      : nullptr;
+  const int64_t nchips = int64_t(r.gx) * r.gy;
+  for (int64_t k = blockIdx.x; k < nchips; k += gridDim.x) {
+    const int64_t cy = k / r.gx, cx = k - cy * r.gx;
+    label_chip<DT, HS>(r, dp, chip, cy, cx, sm, fl, lut);
+  }
+}
+
+template <int DT, bool HS>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_label_generic(Req r, DevParams dp, int chip) {
+  __shared__ __align__(16) ChipStat st;
+  __shared__ uint8_t lut[256];
+  const int64_t nchips = int64_t(r.gx) * r.gy;
+  for (int64_t k = blockIdx.x; k < nchips; k += gridDim.x) {
+    const int64_t cy = k / r.gx, cx = k - cy * r.gx;
+    label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st, lut);
+  }
+}
+
+size_t resident_smem_bytes(int dt, bool hs) {
+  return sizeof(ChipSmem) + ((hs || dt == SIL_U16) ? sizeof(ChipFlags) : 0);
+}
+
+template <int DT, bool HS>
+static cudaError_t launch_one(const Req& r, const DevParams& dp, int chip,
+                              int grid, cudaStream_t s) {
+  if (chip <= kResidentChip) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    const size_t smem = resident_smem_bytes(DT, HS);
+    std::call_once(once, [&] {
+      attr_err = cudaFuncSetAttribute(k_label<DT, HS>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(smem));
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    k_label<DT, HS><<<grid, kThreads, smem, s>>>(r, dp, chip);
+  } else {
+    k_label_generic<DT, HS><<<grid, kThreads, 0, s>>>(r, dp, chip);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_label(const Req& r, int dt, const DevParams& dp, int chip,
+                         int grid, cudaStream_t s) {
+  const bool hs = dp.need_hs != 0;
+  if (dt == SIL_U8)
+    return hs ? launch_one<SIL_U8, true>(r, dp, chip, grid, s)
+              : launch_one<SIL_U8, false>(r, dp, chip, grid, s);
+  return hs ? launch_one<SIL_U16, true>(r, dp, chip, grid, s)
+            : launch_one<SIL_U16, false>(r, dp, chip, grid, s);
+}
+
+// Shape / pointer checks shared by the request entry points.
+sil_status check_request(const void* img, int64_t H, int64_t W, int64_t pitch,
+                         sil_dtype dt, const uint8_t* labels, int64_t lpitch,
+                         const uint64_t* counts) {
+  if (dt != SIL_U8 && dt != SIL_U16) {
+    set_error("dtype %d is not SIL_U8 or SIL_U16", int(dt));
+    return SIL_EINVAL;
+  }
+  if (!img || !counts) {
+    set_error("img and counts must not be NULL");
+    return SIL_EINVAL;
+  }
+  if (H < 1 || W < 1 || H > (int64_t(1) << 31) || W > (int64_t(1) << 31) ||
+      H * W >= (int64_t(1) << 40)) {
+    set_error("bad shape %lld x %lld", (long long)H, (long long)W);
+    return SIL_EINVAL;
+  }
+  const int64_t bpp = dt == SIL_U8 ? 3 : 6;
+  if (pitch < W * bpp) {
+    set_error("pitch_bytes %lld < %lld bytes per row", (long long)pitch, (long long)(W * bpp));
+    return SIL_EINVAL;
+  }
+  if (dt == SIL_U16 && ((reinterpret_cast<uintptr_t>(img) & 1) || (pitch & 1))) {
+    set_error("uint16 images need 2-byte aligned img and pitch");
+    return SIL_EINVAL;
+  }
+  if (labels && lpitch < W) {
+    set_error("label_pitch %lld < W %lld", (long long)lpitch, (long long)W);
+    return SIL_EINVAL;
+  }
+  return SIL_OK;
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// ---------------------------------------------------------------------------
+// Confusion counts and colour render (Sec. IV-A metrics; Sec. III-A colours).
+// ---------------------------------------------------------------------------
+__global__ void k_confusion(const uint8_t* pred, int64_t pp, const uint8_t* ref,
+                            int64_t rp, int64_t H, int64_t W, int chip, int gx,
+                            int gy, unsigned long long* conf, uint32_t* chip_conf) {
+  __shared__ uint32_t c16[16];
+  const int64_t nchips = int64_t(gx) * gy;
+  for (int64_t k = blockIdx.x; k < nchips; k += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x < 16) c16[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t cy = k / gx, cx = k - cy * gx;
+    const int64_t y0 = cy * chip, x0 = cx * chip;
+    const int h = int(min(int64_t(chip), H - y0)), w = int(min(int64_t(chip), W - x0));
+    uint32_t loc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) loc[i] = 0;
+    for (int i = threadIdx.x; i < h * w; i += blockDim.x) {
+      const int y = i / w, x = i - y * w;
+      const uint32_t a = pred[(y0 + y) * pp + x0 + x], b = ref[(y0 + y) * rp + x0 + x];
+      if (a > 3 || b > 3) continue;  // not a label: not counted
+      const uint32_t idx = a * 4 + b;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) loc[j] += (idx == uint32_t(j)) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t s = __reduce_add_sync(0xffffffffu, loc[j]);
+      if ((threadIdx.x & 31) == 0 && s) atomicAdd(&c16[j], s);
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+      if (chip_conf) chip_conf[k * 16 + threadIdx.x] = c16[threadIdx.x];
+      atomicAdd(&conf[threadIdx.x], (unsigned long long)c16[threadIdx.x]);
+    }
+  }
+}
+
+__global__ void k_render(const uint8_t* labels, int64_t lp, int64_t H, int64_t W,
+                         uint8_t* rgb, int64_t rp) {
+  // thick ice red, thin ice blue, open water green, masked black
+  const uint32_t pal[4] = {0x0000FFu, 0xFF0000u, 0x00FF00u, 0x000000u};
+  const int64_t n = H * W;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t y = i / W, x = i - y * W;
+    const uint32_t l = labels[y * lp + x];
+    const uint32_t c = pal[l & 3u];
+    uint8_t* o = rgb + y * rp + 3 * x;
+    o[0] = uint8_t(c);
+    o[1] = uint8_t(c >> 8);
+    o[2] = uint8_t(c >> 16);
+  }
+}
+
+}  // namespace sil
+
+using namespace sil;
+
+extern "C" {
+
+sil_status sil_params_default(sil_params* p) {
+  if (!p) {
+    set_error("sil_params_default: NULL");
+    return SIL_EINVAL;
+  }
+  memset(p, 0, sizeof(*p));
+  const uint8_t lo[3][3] = {{0, 0, 205}, {0, 0, 31}, {0, 0, 0}};
+  const uint8_t hi[3][3] = {{185, 255, 255}, {185, 255, 204}, {185, 255, 30}};
+  memcpy(p->lo, lo, sizeof(lo));
+  memcpy(p->hi, hi, sizeof(hi));
+  p->filter = 1;
+  p->chip = 256;
+  p->median = 1;
+  p->mm_min_range = 64;
+  p->mm_min_frac_den = 16;
+  p->v_trunc = 255;
+  p->max_shift = 255;
+  p->bgr = 0;
+  p->u16_scale = 10000;
+  return SIL_OK;
+}
+
+sil_status sil_params_validate(const sil_params* p) {
+  if (!p) {
+    set_error("sil_params_validate: NULL");
+    return SIL_EINVAL;
+  }
+  DevParams dp;
+  return derive_params(p, &dp);
+}
+
+const char* sil_status_string(sil_status s) {
+  switch (s) {
+    case SIL_OK: return "ok";
+    case SIL_EINVAL: return "invalid argument";
+    case SIL_ENOMEM: return "out of memory";
+    case SIL_ECUDA: return "CUDA error";
+    case SIL_ETIMEOUT: return "timed out";
+    case SIL_EBUSY: return "busy";
+    case SIL_ECANCELED: return "cancelled";
+  }
+  return "unknown status";
+}
+
+const char* sil_last_error(void) { return g_err; }
+
+int sil_version(void) { return SIL_ABI_VERSION; }
+
+sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
+                     sil_dtype dt, const sil_params* p, uint8_t* labels,
+                     int64_t label_pitch, uint64_t* counts, uint32_t* chip_counts,
+                     sil_stream stream) {
+  g_err[0] = 0;
+  sil_status st = check_request(img, H, W, pitch_bytes, dt, labels, label_pitch, counts);
+  if (st != SIL_OK) return st;
+  DevParams dp;
+  st = derive_params(p, &dp);
+  if (st != SIL_OK) return st;
+  const int chip = p ? p->chip : 256;
+  Req r;
+  r.img = static_cast<const uint8_t*>(img);
+  r.H = H;
+  r.W = W;
+  r.pitch = pitch_bytes;
+  r.labels = labels;
+  r.lpitch = label_pitch;
+  r.counts = reinterpret_cast<unsigned long long*>(counts);
+  r.chip_counts = chip_counts;
+  r.gx = int32_t((W + chip - 1) / chip);
+  r.gy = int32_t((H + chip - 1) / chip);
+  r.chip_begin = 0;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(uint64_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "sil_label: memset counts");
+  const int64_t nchips = int64_t(r.gx) * r.gy;
+  const int64_t cap = int64_t(device_sm_count()) * 16;
+  const int grid = int(nchips < cap ? nchips : cap);
+  e = launch_label(r, dt, dp, chip, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "sil_label: launch");
+  return SIL_OK;
+}
+
+// Host-buffer variant: per-thread cached device staging buffers.
+struct HostStage {
+  void* img = nullptr;
+  size_t img_bytes = 0;
+  uint8_t* lab = nullptr;
+  size_t lab_bytes = 0;
+  uint64_t* cnt = nullptr;
+  uint32_t* cc = nullptr;
+  size_t cc_bytes = 0;
+  ~HostStage() {
+    cudaFree(img);
+    cudaFree(lab);
+    cudaFree(cnt);
+    cudaFree(cc);
+  }
+};
+static thread_local HostStage g_stage;
+
+static sil_status ensure(void** p, size_t* have, size_t need) {
+  if (*have >= need && *p) return SIL_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(p, need);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+    return SIL_ENOMEM;
+  }
+  *have = need;
+  return SIL_OK;
+}
+
+sil_status sil_label_host(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
+                          sil_dtype dt, const sil_params* p, uint8_t* labels,
+                          int64_t label_pitch, uint64_t* counts,
+                          uint32_t* chip_counts, sil_stream stream) {
+  g_err[0] = 0;
+  sil_status st = check_request(img, H, W, pitch_bytes, dt, labels, label_pitch, counts);
+  if (st != SIL_OK) return st;
+  DevParams dp;
+  st = derive_params(p, &dp);
+  if (st != SIL_OK) return st;
+  const int chip = p ? p->chip : 256;
+  const int64_t bpp = dt == SIL_U8 ? 3 : 6;
+  const int64_t dpitch = ((W * bpp + 127) / 128) * 128;
+  const int64_t gx = (W + chip - 1) / chip, gy = (H + chip - 1) / chip;
+  HostStage& g = g_stage;
+  if ((st = ensure(&g.img, &g.img_bytes, size_t(dpitch * H))) != SIL_OK) return st;
+  if (labels && (st = ensure(reinterpret_cast<void**>(&g.lab), &g.lab_bytes, size_t(W * H))) != SIL_OK)
+    return st;
+  size_t cnt_bytes = g.cnt ? 32 : 0;
+  if ((st = ensure(reinterpret_cast<void**>(&g.cnt), &cnt_bytes, 32)) != SIL_OK) return st;
+  if (chip_counts &&
+      (st = ensure(reinterpret_cast<void**>(&g.cc), &g.cc_bytes, size_t(gx * gy * 16))) != SIL_OK)
+    return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpy2DAsync(g.img, dpitch, img, pitch_bytes, W * bpp, H,
+                                    cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: copy in");
+  st = sil_label(g.img, H, W, dpitch, dt, p, labels ? g.lab : nullptr, W, g.cnt,
+                 chip_counts ? g.cc : nullptr, stream);
+  if (st != SIL_OK) return st;
+  if (labels) {
+    e = cudaMemcpy2DAsync(labels, label_pitch, g.lab, W, W, H, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: copy labels out");
+  }
+  e = cudaMemcpyAsync(counts, g.cnt, 32, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: copy counts out");
+  if (chip_counts) {
+    e = cudaMemcpyAsync(chip_counts, g.cc, size_t(gx * gy * 16), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: copy chip counts out");
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: synchronize");
+  return SIL_OK;
+}
+
+sil_status sil_confusion(const uint8_t* pred, int64_t pred_pitch, const uint8_t* ref,
+                         int64_t ref_pitch, int64_t H, int64_t W, int32_t chip,
+                         uint64_t* conf, uint32_t* chip_conf, sil_stream stream) {
+  g_err[0] = 0;
+  if (!pred || !ref || !conf || H < 1 || W < 1 || pred_pitch < W || ref_pitch < W ||
+      chip < 4 || chip > 512) {
+    set_error("sil_confusion: invalid arguments");
+    return SIL_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(conf, 0, 16 * sizeof(uint64_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "sil_confusion: memset");
+  const int gx = int((W + chip - 1) / chip), gy = int((H + chip - 1) / chip);
+  const int64_t nchips = int64_t(gx) * gy;
+  const int64_t cap = int64_t(device_sm_count()) * 8;
+  k_confusion<<<int(nchips < cap ? nchips : cap), 256, 0, s>>>(
+      pred, pred_pitch, ref, ref_pitch, H, W, chip, gx, gy,
+      reinterpret_cast<unsigned long long*>(conf), chip_conf);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sil_confusion: launch");
+  return SIL_OK;
+}
+
+sil_status sil_render(const uint8_t* labels, int64_t label_pitch, int64_t H, int64_t W,
+                      uint8_t* rgb, int64_t rgb_pitch, sil_stream stream) {
+  g_err[0] = 0;
+  if (!labels || !rgb || H < 1 || W < 1 || label_pitch < W || rgb_pitch < 3 * W) {
+    set_error("sil_render: invalid arguments");
+    return SIL_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = H * W;
+  const int64_t cap = int64_t(device_sm_count()) * 8;
+  const int64_t want = (n + 255) / 256;
+  k_render<<<int(want < cap ? want : cap), 256, 0, s>>>(labels, label_pitch, H, W, rgb, rgb_pitch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sil_render: launch");
+  return SIL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,42 @@
+// sil_common.h -- host/device shared definitions of libsil (not part of the
+// public ABI; the public header is include/sil.h).
+#pragma once
+#include <cstdint>
+
+#include "sil.h"
+
+namespace sil {
+
+// Parameters as the kernels see them (derived once on the host per call).
+struct DevParams {
+  uint8_t lo[3][3];  // [class][H, S, V]
+  uint8_t hi[3][3];
+  int32_t filter, median, mm_min_range, frac_den, v_trunc, max_shift;
+  int32_t bgr;
+  int32_t need_hs;        // 1 if some class range narrows H or S
+  uint64_t u16_mul;       // ceil(2^40 / u16_scale): n / s == (n * mul) >> 40
+  uint32_t u16_half;      // u16_scale / 2
+};
+
+// One labelling request (a tile or a whole scene) as the kernels see it.
+struct Req {
+  const uint8_t* img;
+  int64_t H, W, pitch;
+  uint8_t* labels;        // may be null
+  int64_t lpitch;
+  unsigned long long* counts;  // uint64[4], accumulated with atomics
+  uint32_t* chip_counts;  // may be null
+  int32_t gx, gy;         // chip grid
+  int64_t chip_begin;     // index of this request's first chip in a batch
+};
+
+// Largest chip side handled with the chip resident in shared memory.
+constexpr int kResidentChip = 256;
+constexpr int kThreads = 256;  // 8 warps = 16 half-warp row bands
+
+// Validates p and derives DevParams; returns SIL_OK or SIL_EINVAL with a
+// message stored for sil_last_error().
+sil_status derive_params(const sil_params* p, DevParams* dp);
+void set_error(const char* fmt, ...);
+
+}  // namespace sil
