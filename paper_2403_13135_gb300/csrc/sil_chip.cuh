@@ -44,10 +44,24 @@ struct ChipStat {
   uint32_t nod[kThreads / 32];
   int32_t stat[8];
 };
-struct ChipSmem {
-  uint8_t vf[kResidentChip * kPlaneStride];  // filtered V, plane order
-  ChipStat st;
+// Scratch of the block-wide Otsu search.
+struct alignas(16) StatScratch {
+  uint32_t wc[kThreads / 32], ws[kThreads / 32];
+  uint64_t bnum_lo[kThreads / 32];
+  uint32_t bnum_hi[kThreads / 32], bden[kThreads / 32];
+  int32_t bt[kThreads / 32], lo[kThreads / 32], hi[kThreads / 32];
+  uint32_t n0;
 };
+
+// The statistics come first so the histogram sits at shared offset 0 and a
+// bin's byte offset is its address.
+struct ChipSmem {
+  ChipStat st;
+  StatScratch sc;
+  uint8_t vf[kResidentChip * kPlaneStride];  // filtered V, plane order
+};
+static_assert(sizeof(ChipStat) % 16 == 0 && (sizeof(ChipStat) + sizeof(StatScratch)) % 16 == 0,
+              "plane must stay 16-byte aligned");
 // Per row, per lane: 16 nibbles (bits 0-2 class mask of H/S ranges, bit 3
 // nodata); only used by the uint16 and H/S-narrowed variants.
 struct ChipFlags {
@@ -64,6 +78,38 @@ __device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
 }
 __device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c) {
   return a + b + c - max3(a, b, c) - min3(a, b, c);
+}
+// a * b + c with b a runtime kernel parameter: stays an integer multiply-add.
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  return a * b + c;
+}
+#ifndef SIL_MED_IMAD
+#define SIL_MED_IMAD 0
+#endif
+#ifndef SIL_HIST_IMAD
+#define SIL_HIST_IMAD 0
+#endif
+#ifndef SIL_P2_IMAD
+#define SIL_P2_IMAD 0
+#endif
+// a + b + c - x - y (exact modulo 2^32), on the multiply-add pipe.
+__device__ __forceinline__ uint32_t sum3m2(uint32_t a, uint32_t b, uint32_t c,
+                                           uint32_t x, uint32_t y, const DevParams& dp) {
+#if SIL_MED_IMAD == 1
+  uint32_t s = imad(a, dp.one, b);
+  s = imad(c, dp.one, s);
+  s = imad(x, dp.neg1, s);
+  return imad(y, dp.neg1, s);
+#elif SIL_MED_IMAD == 2
+  return imad(y, dp.neg1, imad(x, dp.neg1, a + b + c));
+#else
+  return a + b + c - x - y;
+#endif
+}
+// median of three packed u16x2 words: 2 min/max + 4 multiply-adds.
+__device__ __forceinline__ uint32_t med3m(uint32_t a, uint32_t b, uint32_t c,
+                                          const DevParams& dp) {
+  return sum3m2(a, b, c, max3(a, b, c), min3(a, b, c), dp);
 }
 
 // ---------------------------------------------------------------------------
@@ -92,6 +138,31 @@ __device__ __forceinline__ void fetch_row(const uint8_t* rowptr, int q, int w,
     else
       raw.v[j] = make_uint4(0, 0, 0, 0);
   }
+}
+
+// Ask L2 to start fetching a chip row that will be decoded a few steps later,
+// so that more of the image is in flight than the registers can hold.  Only
+// 16-byte blocks that contain bytes of the row are named.
+#ifndef SIL_L2PF
+#define SIL_L2PF 0
+#endif
+#ifndef SIL_PFD
+#define SIL_PFD 4
+#endif
+template <int BPP>
+__device__ __forceinline__ void prefetch_row_l2(const uint8_t* rowptr, int q, int w) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(rowptr);
+  const uintptr_t A = a & ~uintptr_t(15);
+  const uint32_t bytes = uint32_t(((a + uintptr_t(BPP) * w + 15) & ~uintptr_t(15)) - A);
+#if SIL_L2PF == 1
+  // one 128-byte line per lane
+  if (uint32_t(q) * 128u < bytes)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(A + uintptr_t(q) * 128u));
+#elif SIL_L2PF == 2
+  // one bulk prefetch per row, issued by the first lane of the band
+  if (q == 0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A), "r"(bytes) : "memory");
+#endif
 }
 
 // u8: pixel j of the segment is bytes 3j..3j+2 after offset M.  For pair
@@ -297,6 +368,103 @@ __device__ __forceinline__ void edge_words(const uint32_t* V, int q, int w,
 // ---------------------------------------------------------------------------
 // Pass 1 for one half-warp band.
 // ---------------------------------------------------------------------------
+// One decoded row of a lane's 16-pixel segment: 8 interleaved words, the two
+// edge words and (uint16 / H-S variants) the per-pixel flags.
+struct RowBuf {
+  uint32_t v[8];
+  uint32_t eL, eR;
+  uint32_t f[2];
+};
+
+// Sorted column (min, median, max) of three packed rows.
+struct Col {
+  uint32_t l, c, x;
+};
+__device__ __forceinline__ Col sort_col(uint32_t a, uint32_t b, uint32_t c,
+                                        const DevParams& dp) {
+  Col r;
+  r.l = min3(a, b, c);
+  r.x = max3(a, b, c);
+  r.c = sum3m2(a, b, c, r.l, r.x, dp);
+  return r;
+}
+
+// Output row y from the window rows (M, Z, P) = (y-1, y, y+1): 3x3 median
+// as med3(max3 of column minima, med3 of column medians, min3 of column
+// maxima), histogram of Vf, Vf plane row.  Column sorts are produced one
+// word ahead of the output that needs them (three live at a time).
+template <bool kFlags, int DT>
+__device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z,
+                                         const RowBuf& P, int y, int q,
+                                         int nvalid, bool use_median,
+                                         const DevParams& dp, ChipSmem& sm,
+                                         ChipFlags* fl, uint32_t& n_nodata) {
+  uint32_t out[8];
+  if (use_median) {
+    Col a = sort_col(M.eL, Z.eL, P.eL, dp);
+    Col b = sort_col(M.v[0], Z.v[0], P.v[0], dp);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const Col c = (i < 7) ? sort_col(M.v[i + 1], Z.v[i + 1], P.v[i + 1], dp)
+                            : sort_col(M.eR, Z.eR, P.eR, dp);
+      const uint32_t lo = max3(a.l, b.l, c.l);
+      const uint32_t hi = min3(a.x, b.x, c.x);
+      const uint32_t mi = med3m(a.c, b.c, c.c, dp);
+      out[i] = med3m(lo, mi, hi, dp);
+      a = b;
+      b = c;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) out[i] = Z.v[i];
+  }
+  // Histogram of Vf over valid, non-nodata pixels.
+  char* hist = reinterpret_cast<char*>(sm.st.hist);
+  if (!kFlags && nvalid == 16) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#if SIL_HIST_IMAD
+      const uint32_t c = out[i] & 0xFF00FF00u;
+      const uint32_t a1 = __umulhi(c, dp.k10);
+      const uint32_t a0 = __umulhi(imad(c, dp.k16, 0u), dp.k10);
+#else
+      const uint32_t a0 = (out[i] >> 6) & 0x3FCu;
+      const uint32_t a1 = (out[i] >> 22) & 0x3FCu;
+#endif
+      atomicAdd(reinterpret_cast<uint32_t*>(hist + a0), 1u);
+      atomicAdd(reinterpret_cast<uint32_t*>(hist + a1), 1u);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t a0 = (out[i] >> 6) & 0x3FCu;
+      const uint32_t a1 = (out[i] >> 22) & 0x3FCu;
+      const bool nd0 = kFlags && ((Z.f[0] >> (4 * i + 3)) & 1u);
+      const bool nd1 = kFlags && ((Z.f[1] >> (4 * i + 3)) & 1u);
+      if (i < nvalid && !nd0) atomicAdd(reinterpret_cast<uint32_t*>(hist + a0), 1u);
+      if (i + 8 < nvalid && !nd1) atomicAdd(reinterpret_cast<uint32_t*>(hist + a1), 1u);
+      if (DT == SIL_U16) {
+        n_nodata += (i < nvalid && nd0) ? 1u : 0u;
+        n_nodata += (i + 8 < nvalid && nd1) ? 1u : 0u;
+      }
+    }
+  }
+  // Vf plane (plane order: word k = [c2k, c2k+1, c2k+8, c2k+9]).
+  uint4 pw;
+  pw.x = __byte_perm(out[0], out[1], 0x7351);
+  pw.y = __byte_perm(out[2], out[3], 0x7351);
+  pw.z = __byte_perm(out[4], out[5], 0x7351);
+  pw.w = __byte_perm(out[6], out[7], 0x7351);
+  *reinterpret_cast<uint4*>(&sm.vf[y * kPlaneStride + 16 * q]) = pw;
+  if (kFlags) {
+    fl->f[y][q][0] = Z.f[0];
+    fl->f[y][q][1] = Z.f[1];
+  }
+}
+
+// Pass 1 of one half-warp band: rows r0..r1-1 of the chip.  The band streams
+// rows r0-1 .. r1 (clamped to the chip) through a single decode site; the
+// row after the one being decoded is already in flight.
 template <int DT, bool HS>
 __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch,
                                            int64_t y0, int64_t x0, int h, int w,
@@ -307,105 +475,45 @@ __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch,
   constexpr int NV = RowDec<DT, HS>::NV;
   constexpr bool kFlags = HS || DT == SIL_U16;
   const int nvalid = min(max(w - 16 * q, 0), 16);
-  const uint8_t* col0 = img + x0 * BPP;
-  auto rowp = [&](int y) { return col0 + (y0 + y) * pitch; };
-  auto moff = [&](int y) { return int(reinterpret_cast<uintptr_t>(rowp(y)) & 15); };
   const bool use_median = dp.filter && dp.median;
-
-  uint32_t Vm[8], V0[8], Vp[8];
-  uint32_t F0[2] = {0, 0}, Fp[2] = {0, 0};
-  uint32_t eLm = 0, eRm = 0, eL0 = 0, eR0 = 0, eLp = 0, eRp = 0;
+  // row sequence: max(r0-1,0), r0, r0+1, ..., min(r1, h-1)
+  const int nrows = r1 - r0 + 2;
+  int fy = max(r0 - 1, 0);
+  const uint8_t* fp = img + x0 * BPP + (y0 + fy) * pitch;
+#ifndef SIL_PREFETCH
+#define SIL_PREFETCH 1
+#endif
   Raw<NV> raw;
-
-  // Row r0 and the row above it (clamped).
-  const int ya = max(r0 - 1, 0);
-  if (nvalid > 0) fetch_row<BPP, NV>(rowp(ya), q, w, raw);
-  decode_row<DT, HS>(raw, moff(ya), nvalid, dp, Vm, Fp);
-  edge_words(Vm, q, w, hmask, eLm, eRm);
-  if (ya == r0) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) V0[i] = Vm[i];
-    eL0 = eLm; eR0 = eRm; F0[0] = Fp[0]; F0[1] = Fp[1];
-  } else {
-    if (nvalid > 0) fetch_row<BPP, NV>(rowp(r0), q, w, raw);
-    decode_row<DT, HS>(raw, moff(r0), nvalid, dp, V0, F0);
-    edge_words(V0, q, w, hmask, eL0, eR0);
-  }
-  // Prefetch the row below r0.
-  int ynext = min(r0 + 1, h - 1);
-  if (nvalid > 0) fetch_row<BPP, NV>(rowp(ynext), q, w, raw);
-
-  for (int y = r0; y < r1; ++y) {
-    decode_row<DT, HS>(raw, moff(ynext), nvalid, dp, Vp, Fp);
-    edge_words(Vp, q, w, hmask, eLp, eRp);
-    ynext = min(y + 2, h - 1);
-    if (y + 1 < r1 && nvalid > 0) fetch_row<BPP, NV>(rowp(ynext), q, w, raw);
-
-    uint32_t out[8];
-    if (use_median) {
-      uint32_t L[10], M[10], X[10];
-#define SIL_SORT3(k, a, b, c)                 \
-  {                                           \
-    L[k] = min3(a, b, c);                     \
-    X[k] = max3(a, b, c);                     \
-    M[k] = (a) + (b) + (c) - L[k] - X[k];     \
-  }
-      SIL_SORT3(0, eLm, eL0, eLp);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) SIL_SORT3(i + 1, Vm[i], V0[i], Vp[i]);
-      SIL_SORT3(9, eRm, eR0, eRp);
-#undef SIL_SORT3
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint32_t lo = max3(L[i], L[i + 1], L[i + 2]);
-        const uint32_t hi = min3(X[i], X[i + 1], X[i + 2]);
-        const uint32_t mi = med3(M[i], M[i + 1], M[i + 2]);
-        out[i] = med3(lo, mi, hi);
+#if SIL_PREFETCH
+  if (nvalid > 0) fetch_row<BPP, NV>(fp, q, w, raw);
+#endif
+  RowBuf M, Z, P;
+  for (int k = 0; k < nrows; ++k) {
+#if !SIL_PREFETCH
+    if (nvalid > 0) fetch_row<BPP, NV>(fp, q, w, raw);
+#endif
+    decode_row<DT, HS>(raw, int(reinterpret_cast<uintptr_t>(fp) & 15), nvalid, dp, P.v, P.f);
+    edge_words(P.v, q, w, hmask, P.eL, P.eR);
+#if SIL_L2PF
+    if (k + SIL_PFD < nrows && nvalid > 0) {
+      const int py = min(r0 + k + SIL_PFD - 1, h - 1);  // row of element k+PFD
+      prefetch_row_l2<BPP>(img + x0 * BPP + (y0 + py) * pitch, q, w);
+    }
+#endif
+    if (k + 1 < nrows) {
+      const int ny = min(r0 + k, h - 1);  // row index of element k+1
+      if (ny != fy) {
+        fp += pitch;
+        fy = ny;
       }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) out[i] = V0[i];
+#if SIL_PREFETCH
+      if (nvalid > 0) fetch_row<BPP, NV>(fp, q, w, raw);
+#endif
     }
-
-    // Histogram of Vf over valid, non-nodata pixels.
-    if (!kFlags && nvalid == 16) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        atomicAdd(&sm.st.hist[(out[i] >> 8) & 0xFFu], 1u);
-        atomicAdd(&sm.st.hist[out[i] >> 24], 1u);
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const bool nd0 = kFlags && ((F0[0] >> (4 * i + 3)) & 1u);
-        const bool nd1 = kFlags && ((F0[1] >> (4 * i + 3)) & 1u);
-        if (i < nvalid && !nd0) atomicAdd(&sm.st.hist[(out[i] >> 8) & 0xFFu], 1u);
-        if (i + 8 < nvalid && !nd1) atomicAdd(&sm.st.hist[out[i] >> 24], 1u);
-        if (kFlags && DT == SIL_U16) {
-          n_nodata += (i < nvalid && nd0) ? 1u : 0u;
-          n_nodata += (i + 8 < nvalid && nd1) ? 1u : 0u;
-        }
-      }
-    }
-    // Vf plane (plane order: word k = [c2k, c2k+1, c2k+8, c2k+9]).
-    uint4 pw;
-    pw.x = __byte_perm(out[0], out[1], 0x7351);
-    pw.y = __byte_perm(out[2], out[3], 0x7351);
-    pw.z = __byte_perm(out[4], out[5], 0x7351);
-    pw.w = __byte_perm(out[6], out[7], 0x7351);
-    *reinterpret_cast<uint4*>(&sm.vf[y * kPlaneStride + 16 * q]) = pw;
-    if (kFlags) {
-      fl->f[y][q][0] = F0[0];
-      fl->f[y][q][1] = F0[1];
-    }
-
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      Vm[i] = V0[i];
-      V0[i] = Vp[i];
-    }
-    eLm = eL0; eRm = eR0; eL0 = eLp; eR0 = eRp;
-    F0[0] = Fp[0]; F0[1] = Fp[1];
+    if (k >= 2)
+      emit_row<kFlags, DT>(M, Z, P, r0 + k - 2, q, nvalid, use_median, dp, sm, fl, n_nodata);
+    M = Z;
+    Z = P;
   }
 }
 
@@ -515,6 +623,115 @@ __device__ __forceinline__ void chip_stats_warp(ChipStat& sm, const DevParams& d
   }
 }
 
+// The same statistics computed by all 256 threads of the CTA (thread t owns
+// histogram bin t), for chips of at most 65536 pixels: block-wide prefix
+// sums, one score per thread, block-wide argmax.  Scores: D = S_T w - N s
+// < 2^40, num = D^2 < 2^80, den = w (N - w) <= 2^32, cross products
+// < 2^112.  Contains __syncthreads(); every thread of the CTA must call it.
+
+__device__ __forceinline__ bool better(uint64_t nlo_a, uint32_t nhi_a, uint32_t den_a, int t_a,
+                                       uint64_t nlo_b, uint32_t nhi_b, uint32_t den_b, int t_b) {
+  // is candidate a strictly better than b (ties: smaller t)?
+  if (t_a < 0) return false;
+  if (t_b < 0) return true;
+  const unsigned __int128 na = ((unsigned __int128)nhi_a << 64) | nlo_a;
+  const unsigned __int128 nb = ((unsigned __int128)nhi_b << 64) | nlo_b;
+  const unsigned __int128 l = na * den_b, r = nb * den_a;
+  return l > r || (l == r && t_a < t_b);
+}
+
+__device__ __forceinline__ void chip_stats_block(ChipStat& st, StatScratch& sc,
+                                                 const DevParams& dp, uint32_t N) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t hv = st.hist[tid];
+  uint32_t c = hv, s = uint32_t(tid) * hv;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t a = __shfl_up_sync(0xffffffffu, c, off);
+    const uint32_t b = __shfl_up_sync(0xffffffffu, s, off);
+    if (lane >= off) { c += a; s += b; }
+  }
+  const uint32_t nz = __ballot_sync(0xffffffffu, hv != 0);
+  if (lane == 31) { sc.wc[wid] = c; sc.ws[wid] = s; }
+  if (lane == 0) {
+    sc.lo[wid] = nz ? wid * 32 + __ffs(nz) - 1 : 256;
+    sc.hi[wid] = nz ? wid * 32 + 31 - __clz(nz) : -1;
+  }
+  __syncthreads();
+  uint32_t ST = 0, pc = 0, ps = 0;
+  int lo = 256, hi = -1;
+#pragma unroll
+  for (int k = 0; k < kThreads / 32; ++k) {
+    if (k < wid) { pc += sc.wc[k]; ps += sc.ws[k]; }
+    ST += sc.ws[k];
+    lo = min(lo, sc.lo[k]);
+    hi = max(hi, sc.hi[k]);
+  }
+  c += pc;  // pixels with Vf <= tid
+  s += ps;
+  // score of threshold t = tid
+  int t = -1;
+  uint64_t nlo = 0;
+  uint32_t nhi = 0, den = 0;
+  if (tid <= 254 && c > 0 && c < N) {
+    const uint64_t D = uint64_t(ST) * c - uint64_t(N) * s;  // >= 0
+    const unsigned __int128 num = (unsigned __int128)D * D;
+    nlo = uint64_t(num);
+    nhi = uint32_t(num >> 64);
+    den = c * (N - c);
+    t = tid;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint64_t o_lo = __shfl_xor_sync(0xffffffffu, nlo, off);
+    const uint32_t o_hi = __shfl_xor_sync(0xffffffffu, nhi, off);
+    const uint32_t o_d = __shfl_xor_sync(0xffffffffu, den, off);
+    const int o_t = __shfl_xor_sync(0xffffffffu, t, off);
+    if (better(o_lo, o_hi, o_d, o_t, nlo, nhi, den, t)) {
+      nlo = o_lo; nhi = o_hi; den = o_d; t = o_t;
+    }
+  }
+  if (lane == 0) {
+    sc.bnum_lo[wid] = nlo; sc.bnum_hi[wid] = nhi; sc.bden[wid] = den; sc.bt[wid] = t;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int k = lane & 7;
+    nlo = sc.bnum_lo[k]; nhi = sc.bnum_hi[k]; den = sc.bden[k]; t = sc.bt[k];
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+      const uint64_t o_lo = __shfl_xor_sync(0xffffffffu, nlo, off);
+      const uint32_t o_hi = __shfl_xor_sync(0xffffffffu, nhi, off);
+      const uint32_t o_d = __shfl_xor_sync(0xffffffffu, den, off);
+      const int o_t = __shfl_xor_sync(0xffffffffu, t, off);
+      if (better(o_lo, o_hi, o_d, o_t, nlo, nhi, den, t)) {
+        nlo = o_lo; nhi = o_hi; den = o_d; t = o_t;
+      }
+    }
+    if (lane == 0) {
+      if (hi < 0) { lo = 0; hi = 0; }
+      const int tt = t < 0 ? lo : t;
+      st.stat[kStatLo] = lo;
+      st.stat[kStatHi] = hi;
+      st.stat[kStatT] = tt;
+      st.stat[kStatN] = int(N);
+    }
+  }
+  __syncthreads();
+  const int tt = st.stat[kStatT];
+  if (tid == tt) sc.n0 = c;
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t n0 = sc.n0, n1 = N - n0;
+    const int lo2 = st.stat[kStatLo], hi2 = st.stat[kStatHi];
+    st.stat[kStatN0] = int(n0);
+    st.stat[kStatGate] = (hi2 - lo2 >= dp.mm_min_range) &&
+                         (uint64_t(dp.frac_den) * n0 >= N) &&
+                         (uint64_t(dp.frac_den) * n1 >= N) && N > 0;
+  }
+  __syncthreads();
+}
+
 // Label table entry for filtered value vf (thread per value).
 // Non-H/S variant: the label code.  H/S variant: bits 0-2 = classes whose V
 // range holds V', bit 3 = absdiff override.
@@ -563,15 +780,27 @@ __device__ __forceinline__ void store_row16(uint8_t* dst, int nvalid, uint4 lab)
     if (j < nvalid) dst[j] = uint8_t(wv[j >> 2] >> (8 * (j & 3)));
 }
 
+// Byte k of w, zero-extended, on the multiply-add pipe: (w << 8(3-k)) >> 24.
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int k, const DevParams& dp) {
+#if SIL_P2_IMAD == 0
+  return __byte_perm(w, 0, 0x4440 + k);
+#endif
+  if (k == 3) return __umulhi(w, dp.k8);
+  if (k == 2) return __umulhi(imad(w, dp.k8, 0u), dp.k8);
+  if (k == 1) return __umulhi(imad(w, dp.k16, 0u), dp.k8);
+  return w & 0xFFu;
+}
+
 template <int DT, bool HS>
 __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch,
                                            int64_t y0, int64_t x0, int w, int r0,
                                            int r1, int q, const uint8_t* lut,
                                            const ChipSmem& sm, const ChipFlags* fl,
-                                           uint32_t* cnt) {
+                                           uint32_t* cnt, const DevParams& dp) {
   constexpr bool kFlags = HS || DT == SIL_U16;
   const int nvalid = min(max(w - 16 * q, 0), 16);
   if (nvalid == 0) return;
+  uint8_t* dst = labels ? labels + (y0 + r0) * lpitch + x0 + 16 * q : nullptr;
   for (int y = r0; y < r1; ++y) {
     const uint4 pw = *reinterpret_cast<const uint4*>(&sm.vf[y * kPlaneStride + 16 * q]);
     // plane word k holds columns (2k, 2k+1, 2k+8, 2k+9)
@@ -579,10 +808,10 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch,
     uint32_t l[16];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      l[2 * k] = lut[__byte_perm(p[k], 0, 0x4440)];
-      l[2 * k + 1] = lut[__byte_perm(p[k], 0, 0x4441)];
-      l[2 * k + 8] = lut[__byte_perm(p[k], 0, 0x4442)];
-      l[2 * k + 9] = lut[__byte_perm(p[k], 0, 0x4443)];
+      l[2 * k] = lut[byte_of(p[k], 0, dp)];
+      l[2 * k + 1] = lut[byte_of(p[k], 1, dp)];
+      l[2 * k + 8] = lut[byte_of(p[k], 2, dp)];
+      l[2 * k + 9] = lut[byte_of(p[k], 3, dp)];
     }
     if (kFlags) {
       const uint32_t f0 = fl->f[y][q][0], f1 = fl->f[y][q][1];
@@ -603,12 +832,23 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch,
         if (HS && j < nvalid) cnt[lab] += 1;
       }
     }
-    uint4 lab;
-    lab.x = __byte_perm(__byte_perm(l[0], l[1], 0x0040), __byte_perm(l[2], l[3], 0x0040), 0x5410);
-    lab.y = __byte_perm(__byte_perm(l[4], l[5], 0x0040), __byte_perm(l[6], l[7], 0x0040), 0x5410);
-    lab.z = __byte_perm(__byte_perm(l[8], l[9], 0x0040), __byte_perm(l[10], l[11], 0x0040), 0x5410);
-    lab.w = __byte_perm(__byte_perm(l[12], l[13], 0x0040), __byte_perm(l[14], l[15], 0x0040), 0x5410);
-    if (labels) store_row16(labels + (y0 + y) * lpitch + x0 + 16 * q, nvalid, lab);
+    if (dst) {
+      // label bytes in natural column order, assembled by multiply-adds
+      uint4 lab;
+#if SIL_P2_IMAD == 0
+      lab.x = __byte_perm(__byte_perm(l[0], l[1], 0x0040), __byte_perm(l[2], l[3], 0x0040), 0x5410);
+      lab.y = __byte_perm(__byte_perm(l[4], l[5], 0x0040), __byte_perm(l[6], l[7], 0x0040), 0x5410);
+      lab.z = __byte_perm(__byte_perm(l[8], l[9], 0x0040), __byte_perm(l[10], l[11], 0x0040), 0x5410);
+      lab.w = __byte_perm(__byte_perm(l[12], l[13], 0x0040), __byte_perm(l[14], l[15], 0x0040), 0x5410);
+#else
+      lab.x = imad(l[3], dp.k24, imad(l[2], dp.k16, imad(l[1], dp.k8, l[0])));
+      lab.y = imad(l[7], dp.k24, imad(l[6], dp.k16, imad(l[5], dp.k8, l[4])));
+      lab.z = imad(l[11], dp.k24, imad(l[10], dp.k16, imad(l[9], dp.k8, l[8])));
+      lab.w = imad(l[15], dp.k24, imad(l[14], dp.k16, imad(l[13], dp.k8, l[12])));
+#endif
+      store_row16(dst, nvalid, lab);
+      dst += lpitch;
+    }
   }
 }
 
@@ -641,13 +881,14 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp,
     if (lane == 0) sm.st.nod[tid >> 5] = n_nodata;
   }
   __syncthreads();
-  if (tid < 32) {
+  {
     uint32_t nd = 0;
-    if (DT == SIL_U16) nd = (lane < kThreads / 32) ? sm.st.nod[lane] : 0u;
-    nd = __reduce_add_sync(0xffffffffu, nd);
-    chip_stats_warp(sm.st, dp, uint32_t(h * w) - nd);
+    if (DT == SIL_U16) {
+#pragma unroll
+      for (int k = 0; k < kThreads / 32; ++k) nd += sm.st.nod[k];
+    }
+    chip_stats_block(sm.st, sm.sc, dp, uint32_t(h * w) - nd);
   }
-  __syncthreads();
   const uint32_t e = lut_entry<HS>(tid, sm.st, dp);
   lut[tid] = uint8_t(e);
   uint32_t cnt[4] = {0, 0, 0, 0};
@@ -662,7 +903,7 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp,
   }
   __syncthreads();
   if (r0 < r1 && (HS || r.labels))
-    band_pass2<DT, HS>(r.labels, r.lpitch, y0, x0, w, r0, r1, q, lut, sm, fl, cnt);
+    band_pass2<DT, HS>(r.labels, r.lpitch, y0, x0, w, r0, r1, q, lut, sm, fl, cnt, dp);
   if (HS) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
