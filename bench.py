@@ -132,12 +132,13 @@ def aggregate(elapsed_s: float, units: float, world: int, backend_group=None):
     return elapsed_s, units
 
 
-def cpu_baseline(img: np.ndarray, budget_s: float = 12.0):
+def cpu_baseline(img: np.ndarray, budget_s: float = 12.0, seed: int = 0):
     """The oracle as it stands, single thread, on whole chips of the scene
-    until budget_s of CPU time is spent; returns Gpixel/s and the sample."""
+    (at least one) until budget_s of CPU time is spent; returns Gpixel/s and
+    the sample."""
     import oracle
     gy, gx = -(-img.shape[0] // CHIP), -(-img.shape[1] // CHIP)
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(seed)
     order = rng.permutation(gy * gx)
     px = 0
     n = 0
@@ -164,11 +165,13 @@ def run_reference(args):
     times = []
     px_step = 0
     sample = ""
+    per_step = args.ref_budget / max(1, args.steps + args.warmup)
+    px_total, t_total = 0.0, 0.0
     for i in range(args.warmup + args.steps):
-        v, sample = cpu_baseline(img, budget_s=max(2.0, args.ref_budget / max(1, args.steps)))
+        v, sample = cpu_baseline(img, budget_s=per_step, seed=i)
         if i >= args.warmup:
             times.append(v)
-    value = float(np.mean(times)) if times else 0.0
+    value = float(len(times) / np.sum(1.0 / np.array(times))) if times else 0.0
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -303,6 +306,236 @@ def run_sil(args):
     return 0
 
 
+def _crop_tiles(img, shapes, seed=0):
+    """Tiles of the given shapes cut at seeded positions out of a scene (same
+    generator, no per-tile generation cost)."""
+    rng = np.random.default_rng(seed)
+    H, W, _ = img.shape
+    out = []
+    for (h, w, _s) in shapes:
+        h, w = min(h, H), min(w, W)
+        y = int(rng.integers(0, H - h + 1))
+        x = int(rng.integers(0, W - w + 1))
+        out.append(np.ascontiguousarray(img[y:y + h, x:x + w]))
+    return out
+
+
+def _time_cuda(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def run_batch(args):
+    """512 uneven tiles (side in {128..2048}, aspect 1:1-1:2): one persistent
+    launch through a captured graph (default and autotuned schedule) vs one
+    sil_label launch per tile."""
+    import torch
+    import paper_2403_13135_gb300 as sil
+    import synth
+    scene, _ = synth.full_scene(1, SIDE)
+    shapes = synth.uneven_tile_shapes(args.tiles)
+    tiles = _crop_tiles(scene, shapes)
+    npx = sum(t.shape[0] * t.shape[1] for t in tiles)
+    dev = [torch.from_numpy(t).cuda() for t in tiles]
+    labs = [torch.empty(t.shape[:2], dtype=torch.uint8, device="cuda") for t in tiles]
+    cnts = [torch.empty(4, dtype=torch.int64, device="cuda") for _ in tiles]
+    ccs = [torch.empty((-(-t.shape[0] // CHIP), -(-t.shape[1] // CHIP), 4), dtype=torch.int32,
+                       device="cuda") for t in tiles]
+    p = sil.params()
+    stream = torch.cuda.current_stream()
+
+    def per_tile():
+        for d, l, c, cc in zip(dev, labs, cnts, ccs):
+            sil.label(d, p, out_labels=l, out_counts=c, out_chip_counts=cc, chip_counts=True, stream=stream)
+
+    ctx = sil.Context()
+    arr = sil.make_tiles(dev, labs, cnts, ccs)
+    batch = lambda: sil.label_batch(ctx, arr, len(tiles), sil.SIL_U8, p, stream)
+    for _ in range(args.warmup):
+        per_tile()
+    t_tile = _time_cuda(per_tile, args.steps, stream)
+    ref = [c.clone() for c in cnts]
+    for _ in range(args.warmup):
+        batch()
+    t_batch = _time_cuda(batch, args.steps, stream)
+    same = all(torch.equal(a, b) for a, b in zip(ref, cnts))
+    best = sil.autotune(ctx, arr, len(tiles), sil.SIL_U8, p, stream)
+    for _ in range(args.warmup):
+        batch()
+    t_tuned = _time_cuda(batch, args.steps, stream)
+    print(json.dumps({
+        "metric": METRIC, "config": {"workload": f"{len(tiles)} uneven tiles, {npx} px, chip {CHIP}"},
+        "per_tile_launches": {"value": npx / t_tile / 1e9, "unit": UNIT, "ms": t_tile * 1e3},
+        "batched_graph": {"value": npx / t_batch / 1e9, "unit": UNIT, "ms": t_batch * 1e3},
+        "batched_autotuned": {"value": npx / t_tuned / 1e9, "unit": UNIT, "ms": t_tuned * 1e3,
+                              "ctas_per_sm": best},
+        "speedup_vs_per_tile": t_tile / min(t_batch, t_tuned), "counts_identical": bool(same)}))
+    ctx.close()
+    return 0
+
+
+def run_served(args):
+    """Poisson stream of requests (90% square tiles, side U{256..4096}; 10%
+    full scenes) from pinned host memory through the continuous-batching
+    server; throughput and p50/p99 latency per arrival rate.  Label buffers
+    come from a pinned pool; when the pool is empty the client waits for a
+    completion before it submits (back-pressure), which the report counts."""
+    import queue
+    import torch
+    import paper_2403_13135_gb300 as sil
+    import synth
+    scene, _ = synth.full_scene(1, SIDE)
+    rng = np.random.default_rng(4)
+    pool = []
+    for i in range(24):
+        s = int(rng.integers(256, 4097))
+        y, x = (int(v) for v in rng.integers(0, SIDE - s + 1, 2))
+        pool.append(torch.from_numpy(np.ascontiguousarray(scene[y:y + s, x:x + s])).pin_memory().numpy())
+    big = torch.from_numpy(scene).pin_memory().numpy()
+    lab_tiles = queue.Queue()
+    for _ in range(args.label_pool):
+        lab_tiles.put(torch.empty((4096, 4096), dtype=torch.uint8).pin_memory().numpy())
+    lab_scenes = queue.Queue()
+    for _ in range(max(2, args.label_pool // 16)):
+        lab_scenes.put(torch.empty((SIDE, SIDE), dtype=torch.uint8).pin_memory().numpy())
+    results = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        lat, px = [], [0]
+        stalls = 0
+        pending = queue.Queue()
+        with sil.Server(max_inflight=128, max_batch=32, want_labels=True) as srv:
+            def collector():
+                while True:
+                    item = pending.get()
+                    if item is None:
+                        return
+                    rid, n, buf, q = item
+                    r = srv.wait(rid, 600000)
+                    lat.append(r["t_done_ms"] - r["t_submit_ms"])
+                    px[0] += n
+                    q.put(buf)
+            th = threading.Thread(target=collector, daemon=True)
+            th.start()
+            arr = np.random.default_rng(int(rate)).exponential(1.0 / rate, 10 ** 7)
+            t0 = time.perf_counter()
+            t_next, k, n_sub = t0, 0, 0
+            while True:
+                now = time.perf_counter()
+                if now - t0 >= args.served_seconds:
+                    break
+                if t_next > now:
+                    time.sleep(min(t_next - now, 0.001))
+                    continue
+                is_scene = rng.random() < 0.1
+                img = big if is_scene else pool[int(rng.integers(0, len(pool)))]
+                q = lab_scenes if is_scene else lab_tiles
+                if q.empty():
+                    stalls += 1
+                buf = q.get()
+                h, w = img.shape[:2]
+                lab = buf if is_scene else buf.reshape(-1)[:h * w].reshape(h, w)
+                rid = srv.submit(img, lab)
+                pending.put((rid, h * w, buf, q))
+                n_sub += 1
+                t_next += arr[k]
+                k += 1
+            pending.put(None)
+            th.join()
+            t_all = time.perf_counter() - t0
+        lat = np.array(lat)
+        results.append({"rate_req_s": rate, "requests": int(len(lat)), "seconds": t_all,
+                        "throughput_gpx_s": px[0] / t_all / 1e9, "req_s": len(lat) / t_all,
+                        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                        "backpressure_waits": stalls})
+        print(json.dumps({"served": results[-1]}), flush=True)
+    print(json.dumps({"metric": "served labelling: throughput and p50/p99 latency",
+                      "config": {"workload": "Poisson arrivals; 90% square tiles side U{256..4096}, "
+                                             f"10% {SIDE}^2 scenes; pinned host uint8 RGB and labels; "
+                                             f"{args.served_seconds} s per rate"},
+                      "served": results}))
+    return 0
+
+
+def run_sweep(args):
+    """Many full scenes back to back: device-resident batched labelling, and
+    end to end with the host-to-device copy of scene i+1 overlapped with the
+    labelling of scene i; uint8 and uint16 reflectance."""
+    import ctypes
+    import torch
+    import paper_2403_13135_gb300 as sil
+    import synth
+    out = {}
+    for dtname, dtype in (("u8", np.uint8), ("u16", np.uint16)):
+        scenes = [synth.full_scene(2000 + i, SIDE, dtype=dtype)[0] for i in range(args.distinct)]
+        n = args.scenes
+        host = [torch.from_numpy(scenes[i % len(scenes)].view(np.uint8).reshape(SIDE, -1)).pin_memory()
+                for i in range(len(scenes))]
+        bpp = 3 if dtype == np.uint8 else 6
+        dt = sil.SIL_U8 if dtype == np.uint8 else sil.SIL_U16
+        p = sil.params()
+        dbuf = [torch.empty((SIDE, SIDE * bpp), dtype=torch.uint8, device="cuda") for _ in range(2)]
+        lab = [torch.empty((SIDE, SIDE), dtype=torch.uint8, device="cuda") for _ in range(2)]
+        cnt = [torch.empty(4, dtype=torch.int64, device="cuda") for _ in range(n)]
+        s_copy, s_comp = torch.cuda.Stream(), torch.cuda.Stream()
+        ev_copy = [torch.cuda.Event() for _ in range(2)]
+        ev_used = [torch.cuda.Event() for _ in range(2)]
+        # device resident: all distinct scenes on device, labelled n times in one batch
+        dres = [h.cuda() for h in host]
+        labs = [torch.empty((SIDE, SIDE), dtype=torch.uint8, device="cuda") for _ in range(n)]
+        imgs = [dres[i % len(dres)] for i in range(n)]
+        tiles = (sil.sil_tile * n)()
+        for i in range(n):
+            t = tiles[i]
+            t.img = imgs[i].data_ptr(); t.H = SIDE; t.W = SIDE; t.pitch_bytes = SIDE * bpp
+            t.labels = labs[i].data_ptr(); t.label_pitch = SIDE; t.counts = cnt[i].data_ptr(); t.chip_counts = None
+        ctx = sil.Context()
+        st = torch.cuda.current_stream()
+        sil.label_batch(ctx, tiles, n, dt, p, st)
+        t_dev = _time_cuda(lambda: sil.label_batch(ctx, tiles, n, dt, p, st), 3, st)
+        del dres, labs
+        # end to end: double-buffered copy-in / label / labels back
+        hl = [torch.empty((SIDE, SIDE), dtype=torch.uint8).pin_memory() for _ in range(2)]
+        for b in range(2):  # warm the copy paths
+            dbuf[b].copy_(host[b % len(host)], non_blocking=True)
+            hl[b].copy_(lab[b], non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(n):
+            b = i % 2
+            with torch.cuda.stream(s_copy):
+                s_copy.wait_event(ev_used[b])
+                dbuf[b].copy_(host[i % len(host)], non_blocking=True)
+                ev_copy[b].record(s_copy)
+            with torch.cuda.stream(s_comp):
+                s_comp.wait_event(ev_copy[b])
+                sil.check(sil.sil_label(dbuf[b].data_ptr(), SIDE, SIDE, SIDE * bpp, dt, ctypes.byref(p),
+                                        lab[b].data_ptr(), SIDE, cnt[i].data_ptr(), None,
+                                        ctypes.c_void_p(s_comp.cuda_stream)))
+                hl[b].copy_(lab[b], non_blocking=True)
+                ev_used[b].record(s_comp)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        px = n * SIDE * SIDE
+        out[dtname] = {"scenes": n, "distinct_scenes": len(scenes),
+                       "device_resident_gpx_s": px / t_dev / 1e9,
+                       "e2e_gpx_s": px / t_e2e / 1e9,
+                       "h2d_gb_s": px * bpp / t_e2e / 1e9,
+                       "alg_bytes_per_px": bpp + 1,
+                       "device_hbm_gb_s": px * (bpp + 1) / t_dev / 1e9}
+        ctx.close()
+        del dbuf, lab, host
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": METRIC, "config": {"workload": f"throughput sweep of {SIDE}^2 scenes"},
+                      "sweep": out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,9 +548,23 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the labeler (from profiles/)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="scene", choices=["scene", "batch", "served", "sweep"],
+                    help="scene: the headline line; batch/served/sweep: the other workloads")
+    ap.add_argument("--tiles", type=int, default=512)
+    ap.add_argument("--rates", default="50,200,1000,2000")
+    ap.add_argument("--served-seconds", type=float, default=10.0)
+    ap.add_argument("--label-pool", type=int, default=96)
+    ap.add_argument("--scenes", type=int, default=32)
+    ap.add_argument("--distinct", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "batch":
+        return run_batch(args)
+    if args.config == "served":
+        return run_served(args)
+    if args.config == "sweep":
+        return run_sweep(args)
     return run_sil(args)
 
 

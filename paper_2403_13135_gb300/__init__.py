@@ -294,3 +294,80 @@ def render(labels, stream=None):
     check(_lib.sil_render(labels.data_ptr(), labels.stride(0), H, W, rgb.data_ptr(), 3 * W,
                           _stream_handle(stream)))
     return rgb
+
+
+class Server:
+    """Continuous-batching labelling server (sil_server_*).  Images are host
+    numpy arrays (H x W x 3, uint8/uint16; pinned memory gives the fastest
+    copies) kept alive here until their request completes."""
+
+    def __init__(self, dt: int = SIL_U8, p=None, *, device: int = 0, max_inflight: int = 64,
+                 mem_budget: int = 0, max_batch: int = 32, want_labels: bool = True):
+        cfg = sil_server_config()
+        check(_lib.sil_server_config_default(ctypes.byref(cfg)))
+        cfg.device, cfg.max_inflight, cfg.device_mem_budget = device, max_inflight, mem_budget
+        cfg.max_batch, cfg.want_labels = max_batch, int(want_labels)
+        self.dt = dt
+        self.params = _as_params(p)
+        self.handle = ctypes.c_void_p()
+        check(_lib.sil_server_create(ctypes.byref(self.handle), ctypes.byref(cfg), dt,
+                                     ctypes.byref(self.params)))
+        self._keep = {}
+
+    def submit(self, img: np.ndarray, labels: np.ndarray | None = None,
+               chip_counts: np.ndarray | None = None) -> int:
+        H, W = img.shape[:2]
+        rid = _I64(0)
+        check(_lib.sil_server_submit(self.handle, img.ctypes.data, H, W, img.strides[0],
+                                     labels.ctypes.data if labels is not None else None,
+                                     labels.strides[0] if labels is not None else W,
+                                     chip_counts.ctypes.data if chip_counts is not None else None,
+                                     ctypes.byref(rid)))
+        self._keep[rid.value] = (img, labels, chip_counts)
+        return rid.value
+
+    @staticmethod
+    def _result(r: sil_request_result) -> dict:
+        return {"id": r.id, "status": r.status, "counts": [int(c) for c in r.counts],
+                "t_submit_ms": r.t_submit_ms, "t_admit_ms": r.t_admit_ms, "t_done_ms": r.t_done_ms}
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> dict:
+        res = sil_request_result()
+        st = _lib.sil_server_wait(self.handle, rid, int(timeout_ms), ctypes.byref(res))
+        if st == SIL_ETIMEOUT:
+            raise SilError(st, (_lib.sil_last_error() or b"").decode())
+        self._keep.pop(rid, None)
+        out = self._result(res)
+        out["status"] = st
+        return out
+
+    def poll(self, rid: int):
+        res = sil_request_result()
+        st = _lib.sil_server_poll(self.handle, rid, ctypes.byref(res))
+        if st == SIL_EBUSY:
+            return None
+        self._keep.pop(rid, None)
+        out = self._result(res)
+        out["status"] = st
+        return out
+
+    def cancel(self, rid: int) -> int:
+        return _lib.sil_server_cancel(self.handle, rid)
+
+    def close(self):
+        if self.handle:
+            _lib.sil_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,153 @@
+"""Batched (persistent kernel + CUDA graph) and served (continuous batching)
+labelling: results identical to single-request labelling and the oracle,
+alone and in a mix."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sil():
+    import paper_2403_13135_gb300 as m
+    return m
+
+
+def _tiles(n, seed=0, sides=(17, 64, 128, 200, 256, 300, 513)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        H = int(rng.choice(sides))
+        W = int(rng.integers(1, 2 * H))
+        img, _ = synth.scene(H, W, 5000 + i, n_floes=4)
+        out.append(img)
+    return out
+
+
+def _run_batch(sil, ctx, imgs, p=None, dt=None):
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    C = sil._as_params(p).chip
+    labs = [torch.full(im.shape[:2], 255, dtype=torch.uint8, device="cuda") for im in imgs]
+    cnts = [torch.empty(4, dtype=torch.int64, device="cuda") for _ in imgs]
+    ccs = [torch.empty((-(-im.shape[0] // C), -(-im.shape[1] // C), 4), dtype=torch.int32, device="cuda")
+           for im in imgs]
+    tiles = sil.make_tiles(dev, labs, cnts, ccs)
+    sil.label_batch(ctx, tiles, len(imgs), sil.SIL_U8 if dt is None else dt, p)
+    torch.cuda.synchronize()
+    return [l.cpu().numpy() for l in labs], [c.cpu().numpy() for c in cnts], [c.cpu().numpy() for c in ccs]
+
+
+def test_batch_matches_single_and_oracle(sil):
+    imgs = _tiles(24)
+    ctx = sil.Context()
+    labs, cnts, ccs = _run_batch(sil, ctx, imgs)
+    for im, l, c, cc in zip(imgs, labs, cnts, ccs):
+        ol, oc, occ, _ = oracle.label(im)
+        assert int((l != ol).sum()) == 0
+        np.testing.assert_array_equal(c.astype(np.uint64), oc)
+        np.testing.assert_array_equal(cc.astype(np.uint32), occ)
+    ctx.close()
+
+
+def test_batch_graph_replay_and_autotune(sil):
+    imgs = _tiles(12, seed=1)
+    ctx = sil.Context()
+    a = _run_batch(sil, ctx, imgs)
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    labs = [torch.empty(im.shape[:2], dtype=torch.uint8, device="cuda") for im in imgs]
+    cnts = [torch.empty(4, dtype=torch.int64, device="cuda") for _ in imgs]
+    tiles = sil.make_tiles(dev, labs, cnts, None)
+    best = sil.autotune(ctx, tiles, len(imgs))
+    assert best >= 1
+    for _ in range(3):  # the same batch replays its cached graph
+        sil.label_batch(ctx, tiles, len(imgs))
+    torch.cuda.synchronize()
+    for i in range(len(imgs)):
+        assert np.array_equal(labs[i].cpu().numpy(), a[0][i])
+        assert np.array_equal(cnts[i].cpu().numpy(), a[1][i])
+    ctx.close()
+
+
+def test_batch_other_variants(sil):
+    imgs = _tiles(6, seed=2)
+    ctx = sil.Context()
+    for p in ({"chip": 64}, {"chip": 300}, {"lo": [[0, 0, 180], [40, 60, 31], [0, 0, 0]],
+                                            "hi": [[185, 40, 255], [100, 200, 204], [185, 255, 40]]}):
+        labs, cnts, ccs = _run_batch(sil, ctx, imgs, p)
+        for im, l, c in zip(imgs, labs, cnts):
+            ol, oc, _, _ = oracle.label(im, p)
+            assert int((l != ol).sum()) == 0, p
+            np.testing.assert_array_equal(c.astype(np.uint64), oc)
+    imgs16 = [synth.scene(150, 170, 77 + i, n_floes=3, dtype=np.uint16)[0] for i in range(3)]
+    labs, cnts, ccs = _run_batch(sil, ctx, imgs16, None, sil.SIL_U16)
+    for im, l, c in zip(imgs16, labs, cnts):
+        ol, oc, _, _ = oracle.label(im)
+        assert int((l != ol).sum()) == 0
+        np.testing.assert_array_equal(c.astype(np.uint64), oc)
+    ctx.close()
+
+
+def test_server_alone_equals_mix_and_oracle(sil):
+    imgs = _tiles(20, seed=3)
+    # alone: one request at a time
+    alone = []
+    with sil.Server(max_inflight=8) as srv:
+        for im in imgs:
+            lab = np.empty(im.shape[:2], np.uint8)
+            cc = np.zeros((-(-im.shape[0] // 256), -(-im.shape[1] // 256), 4), np.uint32)
+            rid = srv.submit(im, lab, cc)
+            r = srv.wait(rid, 60000)
+            assert r["status"] == sil.SIL_OK
+            alone.append((lab, r["counts"], cc))
+    # in the mix: everything submitted at once, small memory budget so that
+    # admission waits for earlier requests to finish
+    budget = 3 * max(im.nbytes for im in imgs)
+    with sil.Server(max_inflight=6, mem_budget=budget, max_batch=4) as srv:
+        ids, outs = [], []
+        for im in imgs:
+            lab = np.empty(im.shape[:2], np.uint8)
+            cc = np.zeros((-(-im.shape[0] // 256), -(-im.shape[1] // 256), 4), np.uint32)
+            ids.append(srv.submit(im, lab, cc))
+            outs.append((lab, cc))
+        res = [srv.wait(i, 60000) for i in ids]
+    for im, (lab, cc), r, (alab, acnt, acc) in zip(imgs, outs, res, alone):
+        assert r["status"] == sil.SIL_OK
+        assert np.array_equal(lab, alab)
+        assert r["counts"] == acnt
+        assert np.array_equal(cc, acc)
+        ol, oc, occ, _ = oracle.label(im)
+        assert np.array_equal(lab, ol)
+        assert r["counts"] == [int(x) for x in oc]
+        assert r["t_submit_ms"] <= r["t_admit_ms"] <= r["t_done_ms"]
+
+
+def test_server_faults_are_reported(sil):
+    """Host-side failures: a request that can never fit the memory budget,
+    an invalid request, cancelling a queued request, a wait that runs out,
+    an unknown id.  Nothing here faults or stalls the GPU."""
+    img, _ = synth.scene(2000, 2000, 9, n_floes=5)
+    with sil.Server(max_inflight=1, mem_budget=2 * img.nbytes + (1 << 20)) as srv:
+        with pytest.raises(sil.SilError) as e:
+            srv.submit(np.zeros((3000, 3000, 3), np.uint8))  # never fits the budget
+        assert e.value.status == sil.SIL_EBUSY
+        with pytest.raises(sil.SilError) as e:
+            srv.submit(np.zeros((0, 5, 3), np.uint8))       # empty image
+        assert e.value.status == sil.SIL_EINVAL
+        ids = [srv.submit(img) for _ in range(5)]
+        # one slot: the last request is still queued -> it can be cancelled
+        assert srv.cancel(ids[-1]) == sil.SIL_OK
+        # the fourth has not run yet either: a zero-length wait runs out
+        with pytest.raises(sil.SilError) as e:
+            srv.wait(ids[-2], 0)
+        assert e.value.status == sil.SIL_ETIMEOUT
+        for i in ids[:-1]:
+            assert srv.wait(i, 60000)["status"] == sil.SIL_OK
+        assert srv.wait(ids[-1], 60000)["status"] == sil.SIL_ECANCELED
+        assert srv.poll(123456789)["status"] == sil.SIL_EINVAL
+        # requests still queued when the server is closed are cancelled
+        for _ in range(3):
+            srv.submit(img)
