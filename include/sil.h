@@ -171,6 +171,29 @@ void sil_ctx_destroy(sil_ctx* ctx);
 sil_status sil_label_batch(const sil_tile* tiles, int32_t n, sil_dtype dt,
                            const sil_params* p, sil_ctx* ctx, sil_stream stream);
 
+/* Batched labelling that allocates nothing (the paper has no counterpart;
+ * this exists for callers of this library that may not allocate device
+ * memory: code running inside a framework whose caching allocator owns all
+ * device memory, plug-ins and callbacks that must not call cudaMalloc
+ * because it can block or synchronise the device, and hosts with a fixed
+ * device-memory budget set up front).  Same work and results as
+ * sil_label_batch, without a context: the request descriptors, chip prefix
+ * sums and work-queue head live in one fixed device array inside the
+ * library (about 22.5 KB, kept by every GPU that loads the library until
+ * the process exits).
+ *   tiles  host array of n descriptors, 1 <= n <= 256; more is rejected
+ *          with SIL_EINVAL and a message naming the limit.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture.  Every call shares the array and leaves the last call's
+ * descriptors in it (the queue head and each tile's counts are zeroed by
+ * the call itself): calls whose work overlaps on the GPU -- for example on
+ * two streams without ordering between them -- race and must not be made;
+ * calls on one stream are ordered.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Asynchronous on `stream`. */
+sil_status sil_label_batch_noalloc(const sil_tile* tiles, int32_t n, sil_dtype dt,
+                                   const sil_params* p, sil_stream stream);
+
 /* Pick the persistent schedule (CTAs per SM, chip-order policy) for the
  * given batch by timing the candidates on `stream`; the result is cached in
  * ctx and used by later sil_label_batch calls with the same dt.  Blocks

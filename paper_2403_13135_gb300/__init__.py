@@ -93,6 +93,7 @@ _SIGS = {
     "sil_label_batch": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P, _P], _I32),
     "sil_autotune": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P, _P,
                       ctypes.POINTER(_I32)], _I32),
+    "sil_label_batch_noalloc": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P], _I32),
     "sil_server_config_default": ([ctypes.POINTER(sil_server_config)], _I32),
     "sil_server_create": ([ctypes.POINTER(_P), ctypes.POINTER(sil_server_config), _I32,
                            ctypes.POINTER(sil_params)], _I32),
