@@ -96,22 +96,16 @@ static sil_status cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 // Kernels.
 // ---------------------------------------------------------------------------
-#ifndef SIL_MINB
-#define SIL_MINB 2
-#endif
 template <int DT, bool HS>
-__global__ void __launch_bounds__(kThreads, (DT == SIL_U8 && !HS) ? SIL_MINB : 2)
+__global__ void __launch_bounds__(kThreads, (DT == SIL_U8) ? 2 : 1)
     k_label(Req r, DevParams dp, int chip) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
+  extern __shared__ __align__(128) uint8_t smem_raw[];
   __shared__ uint8_t lut[256];
-  ChipSmem& sm = *reinterpret_cast<ChipSmem*>(smem_raw);
-  ChipFlags* fl = (HS || DT == SIL_U16)
-                      ? reinterpret_cast<ChipFlags*>(smem_raw + sizeof(ChipSmem))
-                      : nullptr;
+  ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
   const int64_t nchips = int64_t(r.gx) * r.gy;
   for (int64_t k = blockIdx.x; k < nchips; k += gridDim.x) {
     const int64_t cy = k / r.gx, cx = k - cy * r.gx;
-    label_chip<DT, HS>(r, dp, chip, cy, cx, sm, fl, lut);
+    label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut);
   }
 }
 
@@ -128,7 +122,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 size_t resident_smem_bytes(int dt, bool hs) {
-  return sizeof(ChipSmem) + ((hs || dt == SIL_U16) ? sizeof(ChipFlags) : 0);
+  if (dt == SIL_U8) return hs ? sizeof(ChipSmem<SIL_U8, true>) : sizeof(ChipSmem<SIL_U8, false>);
+  return hs ? sizeof(ChipSmem<SIL_U16, true>) : sizeof(ChipSmem<SIL_U16, false>);
 }
 
 template <int DT, bool HS>

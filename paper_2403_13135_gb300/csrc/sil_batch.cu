@@ -51,11 +51,11 @@ __device__ __forceinline__ int find_tile(const int64_t* prefix, int n, int64_t k
 }
 
 template <int DT, bool HS, bool RESIDENT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, (DT == SIL_U8) ? 2 : 1)
     k_label_batch(const Req* __restrict__ reqs, const int64_t* __restrict__ prefix,
                   int n, DevParams dp, int chip, unsigned long long* head,
                   int dynamic) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
+  extern __shared__ __align__(128) uint8_t smem_raw[];
   __shared__ uint8_t lut[256];
   __shared__ long long s_next;
   __shared__ __align__(16) ChipStat st_generic;
@@ -72,11 +72,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t local = k - prefix[t];
     const int64_t cy = local / r.gx, cx = local - cy * r.gx;
     if (RESIDENT) {
-      ChipSmem& sm = *reinterpret_cast<ChipSmem*>(smem_raw);
-      ChipFlags* fl = (HS || DT == SIL_U16)
-                          ? reinterpret_cast<ChipFlags*>(smem_raw + sizeof(ChipSmem))
-                          : nullptr;
-      label_chip<DT, HS>(r, dp, chip, cy, cx, sm, fl, lut);
+      ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
+      label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut);
     } else {
       label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st_generic, lut);
     }

@@ -36,7 +36,7 @@ struct Req {
 
 // Largest chip side handled with the chip resident in shared memory.
 constexpr int kResidentChip = 256;
-constexpr int kThreads = 256;  // 8 warps = 16 half-warp row bands
+constexpr int kThreads = 384;  // 12 warps = 12 row bands
 
 // Validates p and derives DevParams; returns SIL_OK or SIL_EINVAL with a
 // message stored for sil_last_error().

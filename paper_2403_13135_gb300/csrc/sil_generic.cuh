@@ -78,7 +78,7 @@ __device__ void label_chip_generic(const Req& r, const DevParams& dp, int chip,
   const int w = int(min(int64_t(chip), r.W - x0));
   const int npx = h * w;
   __syncthreads();
-  sm.hist[tid] = 0;
+  if (tid < 256) sm.hist[tid] = 0;
   __syncthreads();
   uint32_t nod = 0;
   for (int i = tid; i < npx; i += kThreads) {
@@ -101,7 +101,7 @@ __device__ void label_chip_generic(const Req& r, const DevParams& dp, int chip,
     chip_stats_warp(sm, dp, uint32_t(npx) - nd);
   }
   __syncthreads();
-  lut[tid] = uint8_t(lut_entry<HS>(tid, sm, dp));
+  if (tid < 256) lut[tid] = uint8_t(lut_entry<HS>(tid, sm, dp));
   __syncthreads();
   uint32_t cnt[4] = {0, 0, 0, 0};
   for (int i = tid; i < npx; i += kThreads) {
@@ -129,15 +129,12 @@ __device__ void label_chip_generic(const Req& r, const DevParams& dp, int chip,
     if (lane == 0) sm.red[tid >> 5][c] = s;
   }
   __syncthreads();
-  if (tid < 32) {
-    const int c = lane & 3, wv = lane >> 2;
-    uint32_t v = sm.red[wv][c];
-#pragma unroll
-    for (int off = 4; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane < 4) {
-      if (r.chip_counts) r.chip_counts[(cy * r.gx + cx) * 4 + c] = v;
-      atomicAdd(&r.counts[c], (unsigned long long)v);
-    }
+  if (tid < 4) {
+    const int c = tid;
+    uint32_t v = 0;
+    for (int k = 0; k < kWarps; ++k) v += sm.red[k][c];
+    if (r.chip_counts) r.chip_counts[(cy * r.gx + cx) * 4 + c] = v;
+    atomicAdd(&r.counts[c], (unsigned long long)v);
   }
 }
 
