@@ -1,12 +1,12 @@
 // sil_chip.cuh -- the fused per-chip labeler (device code).
 //
-// One CTA of 384 threads (12 warps) labels one chip of at most 256 x 256
-// pixels; a persistent CTA loops over chips.
+// One CTA of 256 threads labels one chip of at most 256 x 256 pixels; a
+// persistent CTA loops over chips.
 //
-//   pass 1  each warp owns a band of rows, each lane 8 columns of them.  Rows
-//           arrive through a 4-slot shared-memory ring filled by lane-
-//           contiguous 16-byte asynchronous copies, so three rows per warp
-//           are in flight while one is computed.
+//   pass 1  each half-warp owns a band of rows, each lane 16 columns of them.
+//           Rows arrive through a 3-slot shared-memory ring filled by lane-
+//           contiguous 16-byte asynchronous copies, so two rows per band are
+//           in flight while one is computed.
 //           decode -> V = max(R,G,B) -> 3x3 median of V clamped to the chip
 //           -> histogram of Vf in shared memory, Vf kept in a shared plane.
 //   stats   all threads: lo/hi, exact Otsu threshold (128-bit compares), gate
@@ -24,8 +24,8 @@
 // Pixel values travel through the median as packed u16x2 words whose 16-bit
 // lanes carry the 8-bit value in their HIGH byte (the low byte is a copy and
 // never decides an order), so one __vimax3_u16x2 / __vimin3_u16x2 handles two
-// pixels and three inputs.  A lane's 8 columns are held as 4 words in
-// "interleaved" order: word i = [col i, col i+4], so the horizontal
+// pixels and three inputs.  A lane's 16 columns are held as 8 words in
+// "interleaved" order: word i = [col i, col i+8], so the horizontal
 // neighbours of word i are words i-1 and i+1 and only the two segment edges
 // need a shuffle.  The median of three is a+b+c-max3-min3, exact in 32-bit
 // wrap-around arithmetic because every lane of the result lies in [0,65535].
@@ -39,9 +39,13 @@
 namespace sil {
 
 constexpr int kWarps = kThreads / 32;
+constexpr int kBands = kThreads / 16;  // one row band per half-warp
 constexpr int kPlaneStride = 256;
-constexpr int kRing = 4;  // row slots per warp
-constexpr int kLanePx = 8;
+#ifndef SIL_RING
+#define SIL_RING 3
+#endif
+constexpr int kRing = SIL_RING;  // row slots per band
+constexpr int kLanePx = 16;
 
 // Per-chip statistics scratch (shared memory).
 struct ChipStat {
@@ -72,11 +76,11 @@ template <int BPP, bool FLAGS>
 struct ChipSmemT {
   ChipStat st;
   StatScratch sc;
-  alignas(16) uint8_t ring[kWarps][kRing][Slot<BPP>::kBytes];
+  alignas(16) uint8_t ring[kBands][kRing][Slot<BPP>::kBytes];
   alignas(16) uint8_t vf[256 * kPlaneStride];  // filtered V, plane order
-  // per row, per lane: 8 nibbles (bits 0-2 class mask of the H/S ranges,
+  // per row, per lane: 16 nibbles (bits 0-2 class mask of the H/S ranges,
   // bit 3 nodata); uint16 and H/S-narrowed variants only
-  uint32_t flags[FLAGS ? 256 : 1][FLAGS ? 32 : 1];
+  uint32_t flags[FLAGS ? 256 : 1][FLAGS ? 16 : 1][FLAGS ? 2 : 1];
 };
 
 enum { kStatLo = 0, kStatHi, kStatT, kStatN0, kStatGate, kStatN };
@@ -88,9 +92,32 @@ __device__ __forceinline__ uint32_t max3(uint32_t a, uint32_t b, uint32_t c) {
 __device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
   return __vimin3_u16x2(a, b, c);
 }
+#ifndef SIL_MED_IMAD
+#define SIL_MED_IMAD 2
+#endif
+#ifndef SIL_HIST_IMAD
+#define SIL_HIST_IMAD 0
+#endif
+#ifndef SIL_P2_IMAD
+#define SIL_P2_IMAD 0
+#endif
+// a * b + c with b a runtime kernel parameter: stays an integer multiply-add,
+// which issues on the multiply-add pipe, beside the min/max/permute pipe.
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) { return a * b + c; }
+// a + b + c - x - y, exact modulo 2^32
+__device__ __forceinline__ uint32_t sum3m2(uint32_t a, uint32_t b, uint32_t c, uint32_t x,
+                                           uint32_t y, const DevParams& dp) {
+#if SIL_MED_IMAD == 1
+  return imad(y, dp.neg1, imad(x, dp.neg1, imad(c, dp.one, imad(a, dp.one, b))));
+#elif SIL_MED_IMAD == 2
+  return imad(y, dp.neg1, imad(x, dp.neg1, a + b + c));
+#else
+  return a + b + c - x - y;
+#endif
+}
 // median of three packed u16x2 words
-__device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c) {
-  return a + b + c - max3(a, b, c) - min3(a, b, c);
+__device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c, const DevParams& dp) {
+  return sum3m2(a, b, c, max3(a, b, c), min3(a, b, c), dp);
 }
 
 // round(x * 255 / s) clamped to 255, i.e. floor((255 x + s/2) / s) for the
@@ -103,26 +130,26 @@ __device__ __forceinline__ uint32_t u16_to_v8(uint32_t x, const DevParams& dp) {
 }
 
 // ---------------------------------------------------------------------------
-// Row copies into the ring.  The warp copies the 16-byte blocks [A, E) that
-// contain a chip row (A = row start rounded down, E = row end rounded up)
-// with one 16-byte asynchronous copy per lane and block, lane-contiguous, so
-// each instruction moves 512 consecutive bytes; one commit group per row.
-// A lane waits for its own groups (cp.async.wait_group) and the warp then
-// synchronises, so no thread spins on a flag.
+// Row copies into the ring.  A half-warp copies the 16-byte blocks [A, E)
+// that contain a chip row (A = row start rounded down, E = row end rounded
+// up) with one 16-byte asynchronous copy per lane and block, lane-contiguous;
+// one commit group per row.  A lane waits for its own groups
+// (cp.async.wait_group) and the half-warp then synchronises, so no thread
+// spins on a flag.
 // ---------------------------------------------------------------------------
 template <int SLOT_BYTES>
 __device__ __forceinline__ void copy_row_async(uint8_t* slot, const uint8_t* rowptr,
-                                               int row_bytes, int lane) {
+                                               int row_bytes, int q) {
   const uintptr_t a = reinterpret_cast<uintptr_t>(rowptr);
   const uintptr_t A = a & ~uintptr_t(15);
-  const uintptr_t E = (a + uintptr_t(row_bytes) + 15) & ~uintptr_t(15);
+  const int nvec = int(((a + uintptr_t(row_bytes) + 15) & ~uintptr_t(15)) - A) >> 4;
   const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(slot));
 #pragma unroll
-  for (int t = 0; t < (SLOT_BYTES / 16 + 31) / 32; ++t) {
-    const uintptr_t src = A + 16u * uintptr_t(lane + 32 * t);
-    if (src < E)
+  for (int t = 0; t < (SLOT_BYTES / 16 + 15) / 16; ++t) {
+    const int v = q + 16 * t;
+    if (v < nvec)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                   ::"r"(dst + 16u * uint32_t(lane + 32 * t)), "l"(src) : "memory");
+                   ::"r"(dst + 16u * uint32_t(v)), "l"(A + 16u * uintptr_t(v)) : "memory");
   }
 }
 __device__ __forceinline__ void commit_rows() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -130,54 +157,85 @@ template <int N>
 __device__ __forceinline__ void wait_rows() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------------------
-// Decode of a lane's 8 pixels from a staged row.  The lane's bytes start at
-// slot offset m + 8 BPP q; the words are read from the aligned word below and
-// the byte shift s = m & 3 (the same for all lanes) picks one of 4 gathers.
+// Decode of a lane's 16 pixels from a staged row.  The lane's bytes start at
+// slot offset m + 16 BPP q; the words are read from the aligned word below
+// and the byte shift s = m & 3 (the same for all lanes) picks one of four
+// gathers.
 // ---------------------------------------------------------------------------
-// u8: pixel j is bytes 3j..3j+2 after shift S; pair (j, j+4) is 12 bytes = 3
+// u8: pixel j is bytes 3j..3j+2 after shift S; pair (j, j+8) is 24 bytes = 6
 // words apart at the same byte position, so one PRMT lifts both channel bytes
 // into the high bytes of a u16x2 word.
 template <int S>
 __device__ __forceinline__ void gather_u8(const uint32_t* v, uint32_t* V, uint32_t (*G)[3]) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 8; ++i) {
     uint32_t g[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int b = S + 3 * i + c;
       const int wi = b >> 2, p = b & 3;
       const uint32_t sel = p | (p << 4) | ((4 + p) << 8) | ((4 + p) << 12);
-      g[c] = __byte_perm(v[wi], v[wi + 3], sel);
+      g[c] = __byte_perm(v[wi], v[wi + 6], sel);
       if (G) G[i][c] = g[c];
     }
     V[i] = max3(g[0], g[1], g[2]);
   }
 }
-// u16: pixel j is bytes 6j..6j+5 after shift S (even); pair (j, j+4) is 24
-// bytes = 6 words apart at the same half-word position.
+// u8 from a 16-byte aligned 64-byte window: pixel j is bytes M+3j..M+3j+2
+// (M = 0..15); same pairing as gather_u8.
+template <int M>
+__device__ __forceinline__ void gather_u8w(const uint32_t* v, uint32_t* V, uint32_t (*G)[3]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    uint32_t g[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int b = M + 3 * i + c;
+      const int wi = b >> 2, p = b & 3;
+      const uint32_t sel = p | (p << 4) | ((4 + p) << 8) | ((4 + p) << 12);
+      g[c] = __byte_perm(v[wi], v[wi + 6], sel);
+      if (G) G[i][c] = g[c];
+    }
+    V[i] = max3(g[0], g[1], g[2]);
+  }
+}
+#define SIL_CASE16(F, ...)                                                 \
+  case 0: F<0>(__VA_ARGS__); break; case 1: F<1>(__VA_ARGS__); break;      \
+  case 2: F<2>(__VA_ARGS__); break; case 3: F<3>(__VA_ARGS__); break;      \
+  case 4: F<4>(__VA_ARGS__); break; case 5: F<5>(__VA_ARGS__); break;      \
+  case 6: F<6>(__VA_ARGS__); break; case 7: F<7>(__VA_ARGS__); break;      \
+  case 8: F<8>(__VA_ARGS__); break; case 9: F<9>(__VA_ARGS__); break;      \
+  case 10: F<10>(__VA_ARGS__); break; case 11: F<11>(__VA_ARGS__); break;  \
+  case 12: F<12>(__VA_ARGS__); break; case 13: F<13>(__VA_ARGS__); break;  \
+  case 14: F<14>(__VA_ARGS__); break; default: F<15>(__VA_ARGS__); break;
+#ifndef SIL_DECODE128
+#define SIL_DECODE128 0
+#endif
+// u16: pixel j is bytes 6j..6j+5 after shift S (even); pair (j, j+8) is 48
+// bytes = 12 words apart at the same half-word position.
 template <int S>
 __device__ __forceinline__ void gather_u16(const uint32_t* v, uint32_t* R, uint32_t (*G)[3]) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 8; ++i) {
     uint32_t g[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int b = S + 6 * i + 2 * c;
       const int wi = b >> 2, hh = (b >> 1) & 1;
-      g[c] = __byte_perm(v[wi], v[wi + 6], hh ? 0x7632u : 0x5410u);
+      g[c] = __byte_perm(v[wi], v[wi + 12], hh ? 0x7632u : 0x5410u);
       if (G) G[i][c] = g[c];
     }
     R[i] = max3(g[0], g[1], g[2]);
   }
 }
 
-// Lane value of column j (0..7) of an interleaved segment (16-bit lane).
+// Lane value of column j (0..15) of an interleaved segment (16-bit lane).
 __device__ __forceinline__ uint32_t seg_get(const uint32_t* V, int j) {
   uint32_t r = 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 8; ++i) {
     if (j == i) r = V[i] & 0xFFFFu;
-    if (j == i + 4) r = V[i] >> 16;
+    if (j == i + 8) r = V[i] >> 16;
   }
   return r;
 }
@@ -224,47 +282,64 @@ __device__ __forceinline__ uint32_t hs_mask(int r, int g, int b, const DevParams
 template <int DT>
 struct Px {
   static constexpr int BPP = DT == SIL_U8 ? 3 : 6;
-  static constexpr int NW = DT == SIL_U8 ? 7 : 13;  // words a lane reads
+  static constexpr int NW = DT == SIL_U8 ? 13 : 25;  // words a lane reads
 };
 
-// Decode the lane's 8 pixels of the staged row in `slot` (row data starting
-// at byte m of the slot) into 4 interleaved V words; F = per-pixel flags
-// (nibble j: bits 0-2 H/S class mask, bit 3 nodata) for the variants that
-// need them.
+// Decode the lane's 16 pixels of the staged row in `slot` (row data starting
+// at byte m of the slot) into 8 interleaved V words; F[0], F[1] = per-pixel
+// flags of columns 0-7 / 8-15 (nibble: bits 0-2 H/S class mask, bit 3
+// nodata) for the variants that need them.
 #define SIL_CASE4(F, ...)                                         \
   case 0: F<0>(__VA_ARGS__); break; case 1: F<1>(__VA_ARGS__); break; \
   case 2: F<2>(__VA_ARGS__); break; default: F<3>(__VA_ARGS__); break;
 
 template <int DT, bool HS>
 __device__ __forceinline__ void decode_row(const uint8_t* slot, int m, int q, int nvalid,
-                                           const DevParams& dp, uint32_t* V, uint32_t& F) {
+                                           const DevParams& dp, uint32_t* V, uint32_t* F) {
   constexpr int NW = Px<DT>::NW;
-  const uint32_t* base = reinterpret_cast<const uint32_t*>(slot) + (m >> 2) + 2 * Px<DT>::BPP * q;
-  uint32_t v[NW];
-#pragma unroll
-  for (int k = 0; k < NW; ++k) v[k] = base[k];
-  uint32_t G[4][3];
+  uint32_t G[8][3];
   constexpr bool kNeedG = HS;
-  F = 0;
-  if (DT == SIL_U8) {
+  F[0] = F[1] = 0;
+  if (DT == SIL_U8 && SIL_DECODE128) {
+    // four conflict-free 16-byte reads of the lane's 64-byte window
+    const uint4* w4 = reinterpret_cast<const uint4*>(slot + 48 * q);
+    uint32_t v[16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint4 t = w4[k];
+      v[4 * k] = t.x;
+      v[4 * k + 1] = t.y;
+      v[4 * k + 2] = t.z;
+      v[4 * k + 3] = t.w;
+    }
+    switch (m) { SIL_CASE16(gather_u8w, v, V, kNeedG ? G : nullptr) }
+  } else if (DT == SIL_U8) {
+    const uint32_t* base = reinterpret_cast<const uint32_t*>(slot) + (m >> 2) + 4 * Px<DT>::BPP * q;
+    uint32_t v[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) v[k] = base[k];
     switch (m & 3) { SIL_CASE4(gather_u8, v, V, kNeedG ? G : nullptr) }
   } else {
-    uint32_t R[4];
+    const uint32_t* base = reinterpret_cast<const uint32_t*>(slot) + (m >> 2) + 4 * Px<DT>::BPP * q;
+    uint32_t v[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) v[k] = base[k];
+    uint32_t R[8];
     if (m & 2)
       gather_u16<2>(v, R, kNeedG ? G : nullptr);
     else
       gather_u16<0>(v, R, kNeedG ? G : nullptr);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
       const uint32_t x0 = R[i] & 0xFFFFu, x1 = R[i] >> 16;
       V[i] = (u16_to_v8(x0, dp) << 8) | (u16_to_v8(x1, dp) << 24);
-      F |= (x0 == 0 ? 8u : 0u) << (4 * i);
-      F |= (x1 == 0 ? 8u : 0u) << (4 * (i + 4));
+      F[0] |= (x0 == 0 ? 8u : 0u) << (4 * i);
+      F[1] |= (x1 == 0 ? 8u : 0u) << (4 * i);
     }
   }
   if (HS) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
       int c0[3], c1[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -277,39 +352,40 @@ __device__ __forceinline__ void decode_row(const uint8_t* slot, int m, int q, in
         }
       }
       const int ri = dp.bgr ? 2 : 0, bi = dp.bgr ? 0 : 2;
-      F |= hs_mask(c0[ri], c0[1], c0[bi], dp) << (4 * i);
-      F |= hs_mask(c1[ri], c1[1], c1[bi], dp) << (4 * (i + 4));
+      F[0] |= hs_mask(c0[ri], c0[1], c0[bi], dp) << (4 * i);
+      F[1] |= hs_mask(c1[ri], c1[1], c1[bi], dp) << (4 * i);
     }
   }
-  if (nvalid < 8 && nvalid > 0) {
+  if (nvalid < 16 && nvalid > 0) {
     // replicate the chip's last column into the lane's columns beyond it
     // (the median window is clamped to the chip)
     const uint32_t rep = seg_get(V, nvalid - 1);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
       if (i >= nvalid) V[i] = (V[i] & 0xFFFF0000u) | rep;
-      if (i + 4 >= nvalid) V[i] = (V[i] & 0x0000FFFFu) | (rep << 16);
+      if (i + 8 >= nvalid) V[i] = (V[i] & 0x0000FFFFu) | (rep << 16);
     }
   }
 }
 
-// Edge words of a decoded row: EL = [col -1, col 3], ER = [col 4, col 8],
-// clamped to the chip (replicated border).
-__device__ __forceinline__ void edge_words(const uint32_t* V, int q, int w, uint32_t& EL,
-                                           uint32_t& ER) {
-  const uint32_t up = __shfl_up_sync(0xffffffffu, V[3], 1);
-  const uint32_t dn = __shfl_down_sync(0xffffffffu, V[0], 1);
-  const uint32_t srcL = (q == 0) ? (V[0] << 16) : up;          // hi lane = col -1
-  const uint32_t srcR = (8 * q + 8 >= w) ? (V[3] >> 16) : dn;  // lo lane = col 8
-  EL = __byte_perm(srcL, V[3], 0x5432);
+// Edge words of a decoded row: EL = [col -1, col 7], ER = [col 8, col 16],
+// clamped to the chip (replicated border).  Shuffles stay inside the
+// half-warp (hmask).
+__device__ __forceinline__ void edge_words(const uint32_t* V, int q, int w, uint32_t hmask,
+                                           uint32_t& EL, uint32_t& ER) {
+  const uint32_t up = __shfl_up_sync(hmask, V[7], 1, 16);
+  const uint32_t dn = __shfl_down_sync(hmask, V[0], 1, 16);
+  const uint32_t srcL = (q == 0) ? (V[0] << 16) : up;            // hi lane = col -1
+  const uint32_t srcR = (16 * q + 16 >= w) ? (V[7] >> 16) : dn;  // lo lane = col 16
+  EL = __byte_perm(srcL, V[7], 0x5432);
   ER = __byte_perm(V[0], srcR, 0x5432);
 }
 
-// One decoded row of a lane's 8-pixel segment.
+// One decoded row of a lane's 16-pixel segment.
 struct RowBuf {
-  uint32_t v[4];
+  uint32_t v[8];
   uint32_t eL, eR;
-  uint32_t f;
+  uint32_t f[2];
 };
 
 // Output row y from the window rows (M, Z, P) = (y-1, y, y+1): 3x3 median as
@@ -317,69 +393,84 @@ struct RowBuf {
 // histogram of Vf, Vf plane row.
 template <bool kFlags, int DT, bool FULL, class SM>
 __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const RowBuf& P,
-                                         int y, int q, int nvalid, bool use_median, SM& sm,
-                                         uint32_t& n_nodata) {
-  uint32_t out[4];
+                                         int y, int q, int nvalid, bool use_median,
+                                         const DevParams& dp, SM& sm, uint32_t& n_nodata) {
+  uint32_t out[8];
   if (use_median) {
-    uint32_t L[6], X[6], C[6];
+    uint32_t L[10], X[10], C[10];
 #define SIL_SORT3(k, a, b, c)             \
   {                                       \
     L[k] = min3(a, b, c);                 \
     X[k] = max3(a, b, c);                 \
-    C[k] = (a) + (b) + (c) - L[k] - X[k]; \
+    C[k] = sum3m2(a, b, c, L[k], X[k], dp);  \
   }
     SIL_SORT3(0, M.eL, Z.eL, P.eL);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) SIL_SORT3(i + 1, M.v[i], Z.v[i], P.v[i]);
-    SIL_SORT3(5, M.eR, Z.eR, P.eR);
+    for (int i = 0; i < 8; ++i) SIL_SORT3(i + 1, M.v[i], Z.v[i], P.v[i]);
+    SIL_SORT3(9, M.eR, Z.eR, P.eR);
 #undef SIL_SORT3
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t lo = max3(L[i], L[i + 1], L[i + 2]);
-      const uint32_t hi = min3(X[i], X[i + 1], X[i + 2]);
-      const uint32_t mi = med3(C[i], C[i + 1], C[i + 2]);
-      out[i] = med3(lo, mi, hi);
+    for (int i = 0; i < 8; i += 2) {
+      // outputs i and i+1 share the middle pair of column medians:
+      // med3(x, b, c) = max(min(b, c), min(max(b, c), x))
+      const uint32_t pl = __vminu2(C[i + 1], C[i + 2]), ph = __vmaxu2(C[i + 1], C[i + 2]);
+      const uint32_t mi0 = __vmaxu2(pl, __vminu2(ph, C[i]));
+      const uint32_t mi1 = __vmaxu2(pl, __vminu2(ph, C[i + 3]));
+      out[i] = med3(max3(L[i], L[i + 1], L[i + 2]), mi0, min3(X[i], X[i + 1], X[i + 2]), dp);
+      out[i + 1] = med3(max3(L[i + 1], L[i + 2], L[i + 3]), mi1, min3(X[i + 1], X[i + 2], X[i + 3]), dp);
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) out[i] = Z.v[i];
+    for (int i = 0; i < 8; ++i) out[i] = Z.v[i];
   }
   // Histogram of Vf over valid, non-nodata pixels (byte offset of bin v is
   // 4 v: the value sits in bits 8-15 / 24-31 of each word).
   char* hist = reinterpret_cast<char*>(sm.st.hist);
-  if (!kFlags && (FULL || nvalid == 8)) {
+  if (!kFlags && (FULL || nvalid == 16)) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
+#if SIL_HIST_IMAD
+      // with the copy byte cleared, 4 v_hi = c >> 22 and 4 v_lo = (c << 16) >> 22
+      const uint32_t c = out[i] & 0xFF00FF00u;
+      atomicAdd(reinterpret_cast<uint32_t*>(hist + __umulhi(imad(c, dp.k16, 0u), dp.k10)), 1u);
+      atomicAdd(reinterpret_cast<uint32_t*>(hist + __umulhi(c, dp.k10)), 1u);
+#else
       atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 6) & 0x3FCu)), 1u);
       atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 22) & 0x3FCu)), 1u);
+#endif
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const bool nd0 = kFlags && ((Z.f >> (4 * i + 3)) & 1u);
-      const bool nd1 = kFlags && ((Z.f >> (4 * (i + 4) + 3)) & 1u);
+    for (int i = 0; i < 8; ++i) {
+      const bool nd0 = kFlags && ((Z.f[0] >> (4 * i + 3)) & 1u);
+      const bool nd1 = kFlags && ((Z.f[1] >> (4 * i + 3)) & 1u);
       if (i < nvalid && !nd0) atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 6) & 0x3FCu)), 1u);
-      if (i + 4 < nvalid && !nd1) atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 22) & 0x3FCu)), 1u);
+      if (i + 8 < nvalid && !nd1) atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 22) & 0x3FCu)), 1u);
       if (DT == SIL_U16) {
         n_nodata += (i < nvalid && nd0) ? 1u : 0u;
-        n_nodata += (i + 4 < nvalid && nd1) ? 1u : 0u;
+        n_nodata += (i + 8 < nvalid && nd1) ? 1u : 0u;
       }
     }
   }
-  // Vf plane (plane order: [c0 c1 c4 c5] [c2 c3 c6 c7])
-  uint2 pw;
+  // Vf plane (plane order: word k = [c2k, c2k+1, c2k+8, c2k+9])
+  uint4 pw;
   pw.x = __byte_perm(out[0], out[1], 0x7351);
   pw.y = __byte_perm(out[2], out[3], 0x7351);
-  *reinterpret_cast<uint2*>(&sm.vf[y * kPlaneStride + 8 * q]) = pw;
-  if (kFlags) sm.flags[y][q] = Z.f;
+  pw.z = __byte_perm(out[4], out[5], 0x7351);
+  pw.w = __byte_perm(out[6], out[7], 0x7351);
+  *reinterpret_cast<uint4*>(&sm.vf[y * kPlaneStride + 16 * q]) = pw;
+  if (kFlags) {
+    sm.flags[y][q][0] = Z.f[0];
+    sm.flags[y][q][1] = Z.f[1];
+  }
 }
 
-// Pass 1 of one warp's band: output rows r0..r1-1 of the chip.  The band
-// streams rows e(k) = clamp(r0 + k - 1, 0, h - 1), k = 0 .. r1 - r0 + 1,
-// through the warp's ring of kRing row slots, kRing - 1 rows ahead of the
-// one being decoded.  FULL: every lane has 8 columns (chip width 256).
+// Pass 1 of one half-warp's band: output rows r0..r1-1 of the chip.  The
+// band streams rows e(k) = clamp(r0 + k - 1, 0, h - 1), k = 0 .. r1 - r0 + 1,
+// through its ring of kRing row slots, kRing - 1 rows ahead of the one being
+// decoded.  FULL: every lane has 16 columns (chip width 256).
 #ifndef SIL_ROTATE3
-#define SIL_ROTATE3 1
+#define SIL_ROTATE3 0
 #endif
 template <int DT, bool HS, bool FULL, class SM>
 __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, int64_t y0,
@@ -388,13 +479,14 @@ __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, in
   constexpr int BPP = Px<DT>::BPP;
   constexpr bool kFlags = HS || DT == SIL_U16;
   constexpr int SB = Slot<BPP>::kBytes;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int q = lane;
-  const int nvalid = FULL ? 8 : min(max(w - 8 * q, 0), 8);
+  const int lane = threadIdx.x & 31, band = threadIdx.x >> 4;
+  const int q = lane & 15;
+  const uint32_t hmask = 0xFFFFu << (lane & 16);
+  const int nvalid = FULL ? 16 : min(max(w - 16 * q, 0), 16);
   const bool use_median = dp.filter && dp.median;
   const int row_bytes = BPP * w;
   const int nrows = r1 - r0 + 2;
-  uint8_t* ring = sm.ring[wid][0];
+  uint8_t* ring = sm.ring[band][0];
   const uint8_t* chip0 = img + x0 * BPP + y0 * pitch;
   // copy cursor: row index and pointer of the next row to copy
   int cy = max(r0 - 1, 0);
@@ -404,21 +496,21 @@ __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, in
   const uint8_t* dptr = cp;
 #pragma unroll
   for (int k = 0; k < kRing; ++k) {
-    if (k < nrows) copy_row_async<SB>(ring + k * SB, cp, row_bytes, lane);
+    if (k < nrows) copy_row_async<SB>(ring + k * SB, cp, row_bytes, q);
     commit_rows();
     const int ny = min(r0 + k, h - 1);  // e(k + 1)
     if (ny != cy) cp += pitch;
     cy = ny;
   }
-  int k = 0;
+  int k = 0, slot_i = 0;
   // one ring step: decode row e(k) into B, refill its slot with e(k + kRing)
   auto step = [&](RowBuf& B) {
-    uint8_t* slot = ring + (k & (kRing - 1)) * SB;
+    uint8_t* slot = ring + slot_i * SB;
     wait_rows<kRing - 1>();  // this lane's copies of row e(k) have landed
-    __syncwarp();            // ... and every other lane's
+    __syncwarp(hmask);       // ... and every other lane's of the band
     decode_row<DT, HS>(slot, int(reinterpret_cast<uintptr_t>(dptr) & 15), q, nvalid, dp, B.v, B.f);
-    __syncwarp();  // the slot is free again
-    if (k + kRing < nrows) copy_row_async<SB>(slot, cp, row_bytes, lane);
+    __syncwarp(hmask);  // the slot is free again
+    if (k + kRing < nrows) copy_row_async<SB>(slot, cp, row_bytes, q);
     commit_rows();
     const int ny = min(r0 + k + kRing, h - 1);  // e(k + kRing + 1)
     if (ny != cy) cp += pitch;
@@ -426,8 +518,9 @@ __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, in
     const int nd = min(r0 + k, h - 1);  // e(k + 1)
     if (nd != dy) dptr += pitch;
     dy = nd;
-    edge_words(B.v, q, w, B.eL, B.eR);
+    edge_words(B.v, q, w, hmask, B.eL, B.eR);
     ++k;
+    slot_i = (slot_i == kRing - 1) ? 0 : slot_i + 1;
   };
   RowBuf M, Z, P;
   step(M);
@@ -436,22 +529,22 @@ __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, in
   int y = r0;
   for (; y + 3 <= r1; y += 3) {
     step(P);
-    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, sm, n_nodata);
+    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, dp, sm, n_nodata);
     step(M);
-    emit_row<kFlags, DT, FULL>(Z, P, M, y + 1, q, nvalid, use_median, sm, n_nodata);
+    emit_row<kFlags, DT, FULL>(Z, P, M, y + 1, q, nvalid, use_median, dp, sm, n_nodata);
     step(Z);
-    emit_row<kFlags, DT, FULL>(P, M, Z, y + 2, q, nvalid, use_median, sm, n_nodata);
+    emit_row<kFlags, DT, FULL>(P, M, Z, y + 2, q, nvalid, use_median, dp, sm, n_nodata);
   }
   for (; y < r1; ++y) {
     step(P);
-    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, sm, n_nodata);
+    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, dp, sm, n_nodata);
     M = Z;
     Z = P;
   }
 #else
   for (int y = r0; y < r1; ++y) {
     step(P);
-    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, sm, n_nodata);
+    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, dp, sm, n_nodata);
     M = Z;
     Z = P;
   }
@@ -723,50 +816,62 @@ __device__ __forceinline__ uint32_t lut_entry(int vf, const ChipStat& sm,
 // ---------------------------------------------------------------------------
 // Pass 2: Vf plane -> labels (+ per-pixel counts for the H/S variant).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void store_row8(uint8_t* dst, int nvalid, uint32_t a, uint32_t b) {
-  const uintptr_t p = reinterpret_cast<uintptr_t>(dst);
-  if (nvalid == 8) {
-    if ((p & 7) == 0) {
-      *reinterpret_cast<uint2*>(dst) = make_uint2(a, b);
+__device__ __forceinline__ void store_row16(uint8_t* dst, int nvalid, uint4 lab) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+  if (nvalid == 16) {
+    if ((a & 15) == 0) {
+      *reinterpret_cast<uint4*>(dst) = lab;
       return;
     }
-    if ((p & 3) == 0) {
-      reinterpret_cast<uint32_t*>(dst)[0] = a;
-      reinterpret_cast<uint32_t*>(dst)[1] = b;
+    if ((a & 3) == 0) {
+      uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+      d[0] = lab.x;
+      d[1] = lab.y;
+      d[2] = lab.z;
+      d[3] = lab.w;
       return;
     }
   }
+  const uint32_t wv[4] = {lab.x, lab.y, lab.z, lab.w};
 #pragma unroll
-  for (int j = 0; j < 8; ++j)
-    if (j < nvalid) dst[j] = uint8_t((j < 4 ? a : b) >> (8 * (j & 3)));
+  for (int j = 0; j < 16; ++j)
+    if (j < nvalid) dst[j] = uint8_t(wv[j >> 2] >> (8 * (j & 3)));
 }
 
 template <int DT, bool HS, class SM>
 __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int64_t y0, int64_t x0,
                                            int w, int r0, int r1, const uint8_t* lut, const SM& sm,
-                                           uint32_t* cnt) {
+                                           uint32_t* cnt, const DevParams& dp) {
   constexpr bool kFlags = HS || DT == SIL_U16;
-  const int q = threadIdx.x & 31;
-  const int nvalid = min(max(w - 8 * q, 0), 8);
+  const int q = threadIdx.x & 15;
+  const int nvalid = min(max(w - 16 * q, 0), 16);
   if (nvalid == 0) return;
-  uint8_t* dst = labels ? labels + (y0 + r0) * lpitch + x0 + 8 * q : nullptr;
+  uint8_t* dst = labels ? labels + (y0 + r0) * lpitch + x0 + 16 * q : nullptr;
   for (int y = r0; y < r1; ++y) {
-    const uint2 pw = *reinterpret_cast<const uint2*>(&sm.vf[y * kPlaneStride + 8 * q]);
-    // plane words: [c0 c1 c4 c5] [c2 c3 c6 c7]
-    uint32_t l[8];
-    l[0] = lut[__byte_perm(pw.x, 0, 0x4440)];
-    l[1] = lut[__byte_perm(pw.x, 0, 0x4441)];
-    l[4] = lut[__byte_perm(pw.x, 0, 0x4442)];
-    l[5] = lut[__byte_perm(pw.x, 0, 0x4443)];
-    l[2] = lut[__byte_perm(pw.y, 0, 0x4440)];
-    l[3] = lut[__byte_perm(pw.y, 0, 0x4441)];
-    l[6] = lut[__byte_perm(pw.y, 0, 0x4442)];
-    l[7] = lut[__byte_perm(pw.y, 0, 0x4443)];
-    if (kFlags) {
-      const uint32_t f = sm.flags[y][q];
+    const uint4 pw = *reinterpret_cast<const uint4*>(&sm.vf[y * kPlaneStride + 16 * q]);
+    // plane word k holds columns (2k, 2k+1, 2k+8, 2k+9)
+    const uint32_t p[4] = {pw.x, pw.y, pw.z, pw.w};
+    uint32_t l[16];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint32_t fj = (f >> (4 * j)) & 0xFu;
+    for (int k = 0; k < 4; ++k) {
+#if SIL_P2_IMAD
+      // byte b of a word on the multiply-add pipe: (w << 8 (3 - b)) >> 24
+      l[2 * k] = lut[p[k] & 0xFFu];
+      l[2 * k + 1] = lut[__umulhi(imad(p[k], dp.k16, 0u), dp.k8)];
+      l[2 * k + 8] = lut[__umulhi(imad(p[k], dp.k8, 0u), dp.k8)];
+      l[2 * k + 9] = lut[__umulhi(p[k], dp.k8)];
+#else
+      l[2 * k] = lut[__byte_perm(p[k], 0, 0x4440)];
+      l[2 * k + 1] = lut[__byte_perm(p[k], 0, 0x4441)];
+      l[2 * k + 8] = lut[__byte_perm(p[k], 0, 0x4442)];
+      l[2 * k + 9] = lut[__byte_perm(p[k], 0, 0x4443)];
+#endif
+    }
+    if (kFlags) {
+      const uint32_t f0 = sm.flags[y][q][0], f1 = sm.flags[y][q][1];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t fj = ((j < 8 ? f0 : f1) >> (4 * (j & 7))) & 0xFu;
         uint32_t lab;
         if (HS) {
           const uint32_t e = l[j];
@@ -782,9 +887,19 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
       }
     }
     if (dst) {
-      const uint32_t a = __byte_perm(__byte_perm(l[0], l[1], 0x0040), __byte_perm(l[2], l[3], 0x0040), 0x5410);
-      const uint32_t b = __byte_perm(__byte_perm(l[4], l[5], 0x0040), __byte_perm(l[6], l[7], 0x0040), 0x5410);
-      store_row8(dst, nvalid, a, b);
+      uint4 lab;
+#if SIL_P2_IMAD
+      lab.x = imad(l[3], dp.k24, imad(l[2], dp.k16, imad(l[1], dp.k8, l[0])));
+      lab.y = imad(l[7], dp.k24, imad(l[6], dp.k16, imad(l[5], dp.k8, l[4])));
+      lab.z = imad(l[11], dp.k24, imad(l[10], dp.k16, imad(l[9], dp.k8, l[8])));
+      lab.w = imad(l[15], dp.k24, imad(l[14], dp.k16, imad(l[13], dp.k8, l[12])));
+#else
+      lab.x = __byte_perm(__byte_perm(l[0], l[1], 0x0040), __byte_perm(l[2], l[3], 0x0040), 0x5410);
+      lab.y = __byte_perm(__byte_perm(l[4], l[5], 0x0040), __byte_perm(l[6], l[7], 0x0040), 0x5410);
+      lab.z = __byte_perm(__byte_perm(l[8], l[9], 0x0040), __byte_perm(l[10], l[11], 0x0040), 0x5410);
+      lab.w = __byte_perm(__byte_perm(l[12], l[13], 0x0040), __byte_perm(l[14], l[15], 0x0040), 0x5410);
+#endif
+      store_row16(dst, nvalid, lab);
       dst += lpitch;
     }
   }
@@ -796,12 +911,12 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
 template <int DT, bool HS, class SM>
 __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, int chip,
                                            int64_t cy, int64_t cx, SM& sm, uint8_t* lut) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, band = tid >> 4;
   const int64_t y0 = cy * chip, x0 = cx * chip;
   const int h = int(min(int64_t(chip), r.H - y0));
   const int w = int(min(int64_t(chip), r.W - x0));
-  // balanced row bands, one per warp
-  const int r0 = (wid * h) / kWarps, r1 = ((wid + 1) * h) / kWarps;
+  // balanced row bands, one per half-warp
+  const int r0 = (band * h) / kBands, r1 = ((band + 1) * h) / kBands;
 
   __syncthreads();  // the previous chip of a persistent CTA is done with sm
   if (tid < 256) sm.st.hist[tid] = 0;
@@ -841,8 +956,29 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
     }
   }
   __syncthreads();
+  // A chip whose every present value maps to one label (common inside a
+  // floe) is filled with that label instead of being looked up pixel by pixel.
+  bool uniform = false;
+  if (!HS) {
+    const int lo = sm.st.stat[kStatLo], hi = sm.st.stat[kStatHi];
+    const bool nodata = uint32_t(sm.st.stat[kStatN]) != uint32_t(h * w);
+    const bool same = (tid >= lo && tid <= hi && tid < 256) ? (lut[tid] == lut[lo]) : true;
+    uniform = __syncthreads_and(same && !nodata) != 0;
+  }
   uint32_t cnt[4] = {0, 0, 0, 0};
-  if (r0 < r1 && (HS || r.labels)) band_pass2<DT, HS>(r.labels, r.lpitch, y0, x0, w, r0, r1, lut, sm, cnt);
+  if (uniform) {
+    if (r0 < r1 && r.labels) {
+      const int q = tid & 15;
+      const int nvalid = min(max(w - 16 * q, 0), 16);
+      const uint32_t cw = uint32_t(lut[sm.st.stat[kStatLo]]) * 0x01010101u;
+      if (nvalid > 0) {
+        uint8_t* dst = r.labels + (y0 + r0) * r.lpitch + x0 + 16 * q;
+        for (int y = r0; y < r1; ++y, dst += r.lpitch) store_row16(dst, nvalid, make_uint4(cw, cw, cw, cw));
+      }
+    }
+  } else if (r0 < r1 && (HS || r.labels)) {
+    band_pass2<DT, HS>(r.labels, r.lpitch, y0, x0, w, r0, r1, lut, sm, cnt, dp);
+  }
   if (HS) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {

@@ -34,9 +34,12 @@ struct Req {
   int64_t chip_begin;     // index of this request's first chip in a batch
 };
 
+#ifndef SIL_THREADS
+#define SIL_THREADS 320
+#endif
 // Largest chip side handled with the chip resident in shared memory.
 constexpr int kResidentChip = 256;
-constexpr int kThreads = 384;  // 12 warps = 12 row bands
+constexpr int kThreads = SIL_THREADS;  // 10 warps = 20 half-warp row bands
 
 // Validates p and derives DevParams; returns SIL_OK or SIL_EINVAL with a
 // message stored for sil_last_error().
