@@ -32,6 +32,10 @@ if ROOT not in sys.path:
 
 SIDE = 10980
 CHIP = 256
+# DRAM bytes (read + write) of one labeler launch on this workload, from the
+# ncu capture summarised in profiles/k_label_u8_scene10980.md; must be
+# re-measured (or set to None) whenever the kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = (361.927424 + 91.827968) * 1e6
 METRIC = "Gpixel/s labeled (bit-exact)"
 UNIT = "Gpixel/s"
 
@@ -545,7 +549,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
-    ap.add_argument("--traffic", type=float, default=None,
+    ap.add_argument("--traffic", type=float, default=TRAFFIC_BYTES_PER_LAUNCH,
                     help="ncu dram bytes per launch of the labeler (from profiles/)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="scene", choices=["scene", "batch", "served", "sweep"],
