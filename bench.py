@@ -33,9 +33,9 @@ if ROOT not in sys.path:
 SIDE = 10980
 CHIP = 256
 # DRAM bytes (read + write) of one labeler launch on this workload, from the
-# ncu capture summarised in profiles/k_label_u8_scene10980.md; must be
-# re-measured (or set to None) whenever the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = (361.927424 + 91.827968) * 1e6
+# ncu capture summarised in profiles/k_label_u8_scene10980.md; None until the
+# current kernel has been captured (it is reset whenever the kernel changes).
+TRAFFIC_BYTES_PER_LAUNCH = None
 METRIC = "Gpixel/s labeled (bit-exact)"
 UNIT = "Gpixel/s"
 

@@ -95,9 +95,6 @@ __device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
 #ifndef SIL_MED_IMAD
 #define SIL_MED_IMAD 2
 #endif
-#ifndef SIL_HIST_IMAD
-#define SIL_HIST_IMAD 0
-#endif
 #ifndef SIL_P2_IMAD
 #define SIL_P2_IMAD 0
 #endif
@@ -288,12 +285,14 @@ struct Px {
 // Decode the lane's 16 pixels of the staged row in `slot` (row data starting
 // at byte m of the slot) into 8 interleaved V words; F[0], F[1] = per-pixel
 // flags of columns 0-7 / 8-15 (nibble: bits 0-2 H/S class mask, bit 3
-// nodata) for the variants that need them.
+// nodata) for the variants that need them.  A4: every row of the chip starts
+// on a 4-byte boundary (m & 3 == 0), so the byte-shift dispatch, whose case
+// can differ between the two half-warps of a warp, is left out.
 #define SIL_CASE4(F, ...)                                         \
   case 0: F<0>(__VA_ARGS__); break; case 1: F<1>(__VA_ARGS__); break; \
   case 2: F<2>(__VA_ARGS__); break; default: F<3>(__VA_ARGS__); break;
 
-template <int DT, bool HS>
+template <int DT, bool HS, bool A4>
 __device__ __forceinline__ void decode_row(const uint8_t* slot, int m, int q, int nvalid,
                                            const DevParams& dp, uint32_t* V, uint32_t* F) {
   constexpr int NW = Px<DT>::NW;
@@ -318,14 +317,17 @@ __device__ __forceinline__ void decode_row(const uint8_t* slot, int m, int q, in
     uint32_t v[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) v[k] = base[k];
-    switch (m & 3) { SIL_CASE4(gather_u8, v, V, kNeedG ? G : nullptr) }
+    if (A4)
+      gather_u8<0>(v, V, kNeedG ? G : nullptr);
+    else
+      switch (m & 3) { SIL_CASE4(gather_u8, v, V, kNeedG ? G : nullptr) }
   } else {
     const uint32_t* base = reinterpret_cast<const uint32_t*>(slot) + (m >> 2) + 4 * Px<DT>::BPP * q;
     uint32_t v[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) v[k] = base[k];
     uint32_t R[8];
-    if (m & 2)
+    if (!A4 && (m & 2))
       gather_u16<2>(v, R, kNeedG ? G : nullptr);
     else
       gather_u16<0>(v, R, kNeedG ? G : nullptr);
@@ -423,29 +425,22 @@ __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const
 #pragma unroll
     for (int i = 0; i < 8; ++i) out[i] = Z.v[i];
   }
-  // Histogram of Vf over valid, non-nodata pixels (byte offset of bin v is
-  // 4 v: the value sits in bits 8-15 / 24-31 of each word).
-  char* hist = reinterpret_cast<char*>(sm.st.hist);
+  // Histogram of Vf over valid, non-nodata pixels; the bin index is byte 1
+  // (low lane) or byte 3 (high lane) of each word.
+  uint32_t* hist = sm.st.hist;
   if (!kFlags && (FULL || nvalid == 16)) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-#if SIL_HIST_IMAD
-      // with the copy byte cleared, 4 v_hi = c >> 22 and 4 v_lo = (c << 16) >> 22
-      const uint32_t c = out[i] & 0xFF00FF00u;
-      atomicAdd(reinterpret_cast<uint32_t*>(hist + __umulhi(imad(c, dp.k16, 0u), dp.k10)), 1u);
-      atomicAdd(reinterpret_cast<uint32_t*>(hist + __umulhi(c, dp.k10)), 1u);
-#else
-      atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 6) & 0x3FCu)), 1u);
-      atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 22) & 0x3FCu)), 1u);
-#endif
+      atomicAdd(&hist[__byte_perm(out[i], 0, 0x4441)], 1u);
+      atomicAdd(&hist[__byte_perm(out[i], 0, 0x4443)], 1u);
     }
   } else {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const bool nd0 = kFlags && ((Z.f[0] >> (4 * i + 3)) & 1u);
       const bool nd1 = kFlags && ((Z.f[1] >> (4 * i + 3)) & 1u);
-      if (i < nvalid && !nd0) atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 6) & 0x3FCu)), 1u);
-      if (i + 8 < nvalid && !nd1) atomicAdd(reinterpret_cast<uint32_t*>(hist + ((out[i] >> 22) & 0x3FCu)), 1u);
+      if (i < nvalid && !nd0) atomicAdd(&hist[__byte_perm(out[i], 0, 0x4441)], 1u);
+      if (i + 8 < nvalid && !nd1) atomicAdd(&hist[__byte_perm(out[i], 0, 0x4443)], 1u);
       if (DT == SIL_U16) {
         n_nodata += (i < nvalid && nd0) ? 1u : 0u;
         n_nodata += (i + 8 < nvalid && nd1) ? 1u : 0u;
@@ -468,11 +463,12 @@ __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const
 // Pass 1 of one half-warp's band: output rows r0..r1-1 of the chip.  The
 // band streams rows e(k) = clamp(r0 + k - 1, 0, h - 1), k = 0 .. r1 - r0 + 1,
 // through its ring of kRing row slots, kRing - 1 rows ahead of the one being
-// decoded.  FULL: every lane has 16 columns (chip width 256).
+// decoded.  FULL: every lane has 16 columns (chip width 256).  A4: every row
+// of the chip starts on a 4-byte boundary.
 #ifndef SIL_ROTATE3
 #define SIL_ROTATE3 0
 #endif
-template <int DT, bool HS, bool FULL, class SM>
+template <int DT, bool HS, bool FULL, bool A4, class SM>
 __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, int64_t y0,
                                            int64_t x0, int h, int w, int r0, int r1,
                                            const DevParams& dp, SM& sm, uint32_t& n_nodata) {
@@ -508,7 +504,7 @@ __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, in
     uint8_t* slot = ring + slot_i * SB;
     wait_rows<kRing - 1>();  // this lane's copies of row e(k) have landed
     __syncwarp(hmask);       // ... and every other lane's of the band
-    decode_row<DT, HS>(slot, int(reinterpret_cast<uintptr_t>(dptr) & 15), q, nvalid, dp, B.v, B.f);
+    decode_row<DT, HS, A4>(slot, int(reinterpret_cast<uintptr_t>(dptr) & 15), q, nvalid, dp, B.v, B.f);
     __syncwarp(hmask);  // the slot is free again
     if (k + kRing < nrows) copy_row_async<SB>(slot, cp, row_bytes, q);
     commit_rows();
@@ -923,10 +919,20 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
   __syncthreads();
   uint32_t n_nodata = 0;
   if (r0 < r1) {
-    if (w == 256)
-      band_pass1<DT, HS, true>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
-    else
-      band_pass1<DT, HS, false>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+    // rows start on 4-byte boundaries when the base, the pitch and the chip's
+    // first column (x0 * 3 or x0 * 6 bytes) do
+    const bool a4 = ((reinterpret_cast<uintptr_t>(r.img) | uint64_t(r.pitch) | uint64_t(x0)) & 3) == 0;
+    if (w == 256) {
+      if (a4)
+        band_pass1<DT, HS, true, true>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+      else
+        band_pass1<DT, HS, true, false>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+    } else {
+      if (a4)
+        band_pass1<DT, HS, false, true>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+      else
+        band_pass1<DT, HS, false, false>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+    }
   }
   if (DT == SIL_U16) {
     n_nodata = __reduce_add_sync(0xffffffffu, n_nodata);
