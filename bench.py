@@ -33,9 +33,9 @@ if ROOT not in sys.path:
 SIDE = 10980
 CHIP = 256
 # DRAM bytes (read + write) of one labeler launch on this workload, from the
-# ncu capture summarised in profiles/k_label_u8_scene10980.md; None until the
-# current kernel has been captured (it is reset whenever the kernel changes).
-TRAFFIC_BYTES_PER_LAUNCH = None
+# ncu capture summarised in profiles/k_label_u8_scene10980.md; reset to None
+# whenever the kernel changes, until it is captured again.
+TRAFFIC_BYTES_PER_LAUNCH = (361.795072 + 92.403200) * 1e6
 METRIC = "Gpixel/s labeled (bit-exact)"
 UNIT = "Gpixel/s"
 
@@ -159,6 +159,70 @@ def cpu_baseline(img: np.ndarray, budget_s: float = 12.0, seed: int = 0):
     return px / dt / 1e9, f"{n} random 256x256 chips of the scene ({px} px) in {dt:.1f} s"
 
 
+def _chip_worker(task):
+    """Pool worker: the oracle on whole chips of the shared scene until the
+    budget is spent; returns (pixels, chips)."""
+    name, shape, chips, budget_s = task
+    from multiprocessing import shared_memory
+    import oracle
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        img = np.ndarray(shape, dtype=np.uint8, buffer=shm.buf)
+        px, n = 0, 0
+        t0 = time.perf_counter()
+        for cy, cx in chips:
+            crop = np.ascontiguousarray(img[cy * CHIP:(cy + 1) * CHIP, cx * CHIP:(cx + 1) * CHIP])
+            oracle.label(crop)
+            px += crop.shape[0] * crop.shape[1]
+            n += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        del img, crop
+    finally:
+        shm.close()
+    return px, n
+
+
+def _worker_ready(_):
+    import oracle  # noqa: F401  (load the library once per worker)
+    return os.getpid()
+
+
+class OraclePool:
+    """The oracle, unchanged, run on every host core: one single-threaded
+    worker process per core, each labelling its own random whole chips of the
+    scene (shared memory, no copies).  Workers are spawned, never forked, so
+    a CUDA context in the parent is not inherited."""
+
+    def __init__(self, img: np.ndarray, cores: int | None = None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        self.cores = int(cores or len(os.sched_getaffinity(0)))
+        self.shape = img.shape
+        self.shm = shared_memory.SharedMemory(create=True, size=img.nbytes)
+        np.ndarray(img.shape, dtype=np.uint8, buffer=self.shm.buf)[...] = img
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_worker_ready, range(self.cores), chunksize=1)
+
+    def run(self, budget_s: float, seed: int = 0):
+        gy, gx = -(-self.shape[0] // CHIP), -(-self.shape[1] // CHIP)
+        order = np.random.default_rng(seed).permutation(gy * gx)
+        chips = [divmod(int(k), gx) for k in order]
+        tasks = [(self.shm.name, self.shape, chips[i::self.cores], budget_s) for i in range(self.cores)]
+        t0 = time.perf_counter()
+        res = self.pool.map(_chip_worker, tasks, chunksize=1)
+        dt = time.perf_counter() - t0
+        px, n = sum(r[0] for r in res), sum(r[1] for r in res)
+        return px / dt / 1e9, (f"{n} random 256x256 chips of the scene ({px} px) on {self.cores} "
+                               f"worker processes in {dt:.3f} s wall")
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.shm.close()
+        self.shm.unlink()
+
+
 def run_reference(args):
     """The oracle on the host cores (rank 0 only), same metric and workload."""
     ws, rank, local = _dist()
@@ -167,14 +231,16 @@ def run_reference(args):
     import synth
     img, _ = synth.full_scene(1, SIDE)
     times = []
-    px_step = 0
     sample = ""
     per_step = args.ref_budget / max(1, args.steps + args.warmup)
-    px_total, t_total = 0.0, 0.0
-    for i in range(args.warmup + args.steps):
-        v, sample = cpu_baseline(img, budget_s=per_step, seed=i)
-        if i >= args.warmup:
-            times.append(v)
+    pool = OraclePool(img, args.cpu_cores or None)
+    try:
+        for i in range(args.warmup + args.steps):
+            v, sample = pool.run(per_step, seed=i)
+            if i >= args.warmup:
+                times.append(v)
+    finally:
+        pool.close()
     value = float(len(times) / np.sum(1.0 / np.array(times))) if times else 0.0
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
@@ -184,7 +250,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": f"one {SIDE}x{SIDE} uint8 RGB scene, chip {CHIP}, seed 1",
                    "l2": "input larger than L2"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                          "sample": f"per step: {sample}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -301,9 +367,15 @@ def run_sil(args):
             "clocks": clocks,
         }
         if not args.no_cpu_baseline and ws >= 1:
-            v, sample = cpu_baseline(img, args.cpu_budget)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": sample}
+            pool = OraclePool(img, args.cpu_cores or None)
+            try:
+                v, sample = pool.run(args.cpu_budget)
+            finally:
+                pool.close()
+            v1, sample1 = cpu_baseline(img, args.cpu_budget / 2)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                                    "sample": sample,
+                                    "single_core": {"value": v1, "cores": 1, "sample": sample1}}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -552,6 +624,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=TRAFFIC_BYTES_PER_LAUNCH,
                     help="ncu dram bytes per launch of the labeler (from profiles/)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cores", type=int, default=0,
+                    help="oracle worker processes for the CPU baseline (0 = every host core)")
     ap.add_argument("--config", default="scene", choices=["scene", "batch", "served", "sweep"],
                     help="scene: the headline line; batch/served/sweep: the other workloads")
     ap.add_argument("--tiles", type=int, default=512)

@@ -49,3 +49,21 @@ def test_two_rank_aggregation():
     assert el0 == el1 == 2.0                  # max over ranks
     assert u0 == u1 == 64 * 96 + 96 * 96      # sum over ranks
     assert c0 == c1 and sum(c0) == n0 + n1
+
+
+def test_oracle_pool_baseline():
+    """The multi-core CPU baseline: spawned oracle workers share the scene and
+    each labels its own whole chips; every chip is labelled at most once."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    img, _ = synth.scene(600, 520, 7, n_floes=4)
+    pool = bench.OraclePool(img, cores=2)
+    try:
+        v, sample = pool.run(budget_s=0.2, seed=3)
+    finally:
+        pool.close()
+    assert v > 0
+    assert "on 2 worker processes" in sample
+    n = int(sample.split()[0])
+    assert 2 <= n <= 9      # 3 x 3 chips, at least one per worker
