@@ -164,3 +164,59 @@ def uneven_tile(H: int, W: int, seed: int, dtype=np.uint8):
     """One tile of the uneven batch: floes scale with area (at least 3)."""
     n_floes = max(3, int(round(200 * H * W / (10980 * 10980))))
     return scene(H, W, seed, n_floes=n_floes, n_haze=1, n_shadow=1, dtype=dtype)
+
+
+def unet_layer_shapes(F: int = 32, depth: int = 4) -> dict:
+    """Weight shapes of the U-Net (PyTorch layouts) for base width F: name ->
+    (weight shape, kind) with kind 'conv3' (3x3, ReLU), 'up' (2x2 stride-2
+    transposed) or 'head' (1x1 to 3 classes)."""
+    shapes = {}
+    w = [F << l for l in range(depth + 1)]
+    cin = 3
+    for lvl in range(depth):
+        shapes[f"enc{lvl}_0"] = ((w[lvl], cin, 3, 3), "conv3")
+        shapes[f"enc{lvl}_1"] = ((w[lvl], w[lvl], 3, 3), "conv3")
+        cin = w[lvl]
+    shapes["bott_0"] = ((w[depth], w[depth - 1], 3, 3), "conv3")
+    shapes["bott_1"] = ((w[depth], w[depth], 3, 3), "conv3")
+    for lvl in reversed(range(depth)):
+        shapes[f"up{lvl}"] = ((w[lvl + 1], w[lvl], 2, 2), "up")
+        shapes[f"dec{lvl}_0"] = ((w[lvl], 2 * w[lvl], 3, 3), "conv3")
+        shapes[f"dec{lvl}_1"] = ((w[lvl], w[lvl], 3, 3), "conv3")
+    shapes["head"] = ((3, F, 1, 1), "head")
+    return shapes
+
+
+def unet_weights(F: int = 32, depth: int = 4, seed: int = 0) -> dict:
+    """Seeded random U-Net weights (random init; no trained weights exist
+    here).  Every value is k * 2^-m with |k| <= 127, so it is exact in
+    bfloat16: weights k ~ round(32 N(0, 1)) with 2^-m ~ std / 32 for a
+    He-style std (sqrt(2 / fan_in), sqrt(1 / fan_in) without ReLU); biases
+    k / 1024 with k uniform in [-8, 8].  Returns name -> (w, b) float32."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for name, (shape, kind) in unet_layer_shapes(F, depth).items():
+        if kind == "conv3":
+            std = np.sqrt(2.0 / (shape[1] * 9))
+        elif kind == "up":
+            std = np.sqrt(1.0 / shape[0])
+        else:
+            std = np.sqrt(1.0 / shape[1])
+        m = int(round(np.log2(32.0 / std)))
+        k = np.clip(np.round(rng.standard_normal(shape) * 32.0), -127, 127)
+        co = shape[1] if kind == "up" else shape[0]
+        kb = rng.integers(-8, 9, size=co)
+        out[name] = ((k * 2.0 ** -m).astype(np.float32), (kb / 1024.0).astype(np.float32))
+    return out
+
+
+def chips_from_scene(img: np.ndarray, n: int, seed: int = 0, chip: int = 256) -> np.ndarray:
+    """n whole chip x chip crops of an H x W x 3 scene at random chip-grid
+    positions (chips cut as the paper cuts its scenes), [n, chip, chip, 3]."""
+    rng = np.random.default_rng(seed)
+    gy, gx = img.shape[0] // chip, img.shape[1] // chip
+    out = np.empty((n, chip, chip, img.shape[2]), dtype=img.dtype)
+    for i in range(n):
+        cy, cx = int(rng.integers(gy)), int(rng.integers(gx))
+        out[i] = img[cy * chip:(cy + 1) * chip, cx * chip:(cx + 1) * chip]
+    return out
