@@ -1,0 +1,115 @@
+/*
+ * sil_unet.h -- C ABI of the U-Net inference on filtered chips (libsil.so).
+ *
+ * Sec. III-C "U-Net Model Inferencing" of arXiv 2403.13135 cuts the scenes
+ * into 256 x 256 chips, filters them and feeds them to a U-Net that labels
+ * every pixel as a sea-ice class.  The paper names the model (a U-Net,
+ * Sec. III-C "U-Net Model Training") but not its widths, and its trained
+ * weights are not available, so this module runs the network with weights
+ * the caller supplies (random ones in the tests and the benchmark) and is
+ * measured for throughput.  The architecture read from the paper and fixed
+ * here:
+ *
+ *   input    R, G, B bytes of a 256 x 256 chip, each scaled by 1/256
+ *   encoder  for level l = 0..depth-1: two 3x3 convolutions (zero padding
+ *            1, bias, ReLU) of width F 2^l, then 2x2 max pooling
+ *   bottom   two 3x3 convolutions of width F 2^depth
+ *   decoder  for l = depth-1..0: 2x2 stride-2 transposed convolution
+ *            (bias, no activation) to width F 2^l, concatenation
+ *            [upsampled, encoder output of level l], two 3x3 convolutions
+ *   head     1x1 convolution to 3 class scores (float32); label = index of
+ *            the largest score, the first on ties (0 thick ice, 1 thin ice,
+ *            2 open water)
+ *
+ * Every activation is stored as bfloat16 (round to nearest even) in
+ * channels-last layout; products are bfloat16 x bfloat16 summed in float32
+ * on the tensor cores.
+ *
+ * Conventions are those of sil.h: device pointers unless stated otherwise,
+ * asynchronous on the given stream, arguments validated on the host
+ * (SIL_EINVAL, nothing launched), CUDA failures SIL_ECUDA.
+ */
+#ifndef SIL_UNET_H_
+#define SIL_UNET_H_
+
+#include <stdint.h>
+
+#include "sil.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sil_unet sil_unet;
+
+typedef struct sil_unet_config {
+  int32_t base_width; /* F: 16, 32 or 64 (default 32) */
+  int32_t depth;      /* encoder levels: 1..4 (default 4) */
+  int32_t max_batch;  /* chips per sil_unet_forward call: 1..4096 (default 32) */
+} sil_unet_config;
+
+/* Layer kinds of sil_unet_layer_shape. */
+typedef enum sil_unet_layer_kind {
+  SIL_UNET_CONV3 = 0, /* 3x3 conv + ReLU, weight [Co][Ci][3][3] */
+  SIL_UNET_UP = 1,    /* 2x2 stride-2 transposed conv, weight [Ci][Co][2][2] */
+  SIL_UNET_HEAD = 2   /* 1x1 conv to 3 scores, weight [3][F][1][1] */
+} sil_unet_layer_kind;
+
+/* Fills F = 32, depth = 4, max_batch = 32.  SIL_EINVAL on NULL. */
+sil_status sil_unet_config_default(sil_unet_config* cfg);
+
+/* Number of weighted layers: 4 depth + 4 (2 per encoder level, 2 at the
+ * bottom, 3 per decoder level, 1 head); -1 if depth is out of range. */
+int32_t sil_unet_num_layers(int32_t depth);
+
+/* Shape of layer i in this order: enc0_0, enc0_1, enc1_0, ..., bott_0,
+ * bott_1, then for l = depth-1..0: up_l, dec_l_0, dec_l_1; then head.
+ * dims[4] receives the PyTorch weight shape (the first conv has Ci = 3),
+ * *kind its kind; the bias has dims[0] entries (dims[1] for SIL_UNET_UP). */
+sil_status sil_unet_layer_shape(const sil_unet_config* cfg, int32_t i, int64_t dims[4],
+                                int32_t* kind);
+
+/* Multiply-adds x 2 of one chip's forward pass. */
+int64_t sil_unet_flops_per_chip(const sil_unet_config* cfg);
+
+/* Creates a network on `device`: uploads the weights (HOST float32 arrays in
+ * PyTorch layout, one per layer in sil_unet_layer_shape order; values are
+ * rounded to bfloat16 except the head, kept in float32) and allocates the
+ * activations of max_batch chips.  The caller keeps ownership of the host
+ * arrays; the network owns its device memory until sil_unet_destroy.
+ * SIL_EINVAL on a bad config or NULL array, SIL_ENOMEM, SIL_ECUDA. */
+sil_status sil_unet_create(sil_unet** net, const sil_unet_config* cfg,
+                           const float* const* weights, const float* const* biases,
+                           int32_t device);
+void sil_unet_destroy(sil_unet* net);
+
+/* Forward pass of n chips (1..max_batch): chips = DEVICE uint8
+ * [n][256][256][3] (R, G, B); labels = DEVICE uint8 [n][256][256] (nullable);
+ * logits = DEVICE float32 [n][256][256][3] (nullable).  Asynchronous on
+ * `stream`; the network's activations are reused by the next call, so calls
+ * on one network must be ordered (same stream).  Waits inside the kernels
+ * are bounded: a wait that runs out counts an error that
+ * sil_unet_error_count reports. */
+sil_status sil_unet_forward(sil_unet* net, const uint8_t* chips, int32_t n, uint8_t* labels,
+                            float* logits, sil_stream stream);
+
+/* Synchronises the device and returns the number of kernel waits that ran
+ * out since the network was created (0 in normal operation). */
+sil_status sil_unet_error_count(sil_unet* net, uint32_t* count);
+
+/* Output activation of layer i (sil_unet_layer_shape order; i = -1: the
+ * prepared input, 8 channels of which the last 5 are zero) of the last
+ * forward pass: dims = {n, H, W, C} (n of that pass).  The head (the last
+ * layer) keeps no activation: SIL_EINVAL. */
+sil_status sil_unet_tensor_shape(const sil_unet* net, int32_t i, int64_t dims[4]);
+
+/* Copies that activation into DEVICE bfloat16 `dst`, dense [n][H][W][C]
+ * (the network stores encoder outputs inside the decoder's concatenation
+ * buffers, so it is strided in place).  Asynchronous on `stream`. */
+sil_status sil_unet_copy_tensor(const sil_unet* net, int32_t i, void* dst, sil_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIL_UNET_H_ */

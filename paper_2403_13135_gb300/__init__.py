@@ -104,6 +104,17 @@ _SIGS = {
     "sil_server_destroy": ([_P], None),
     "sil_confusion": ([_P, _I64, _P, _I64, _I64, _I64, _I32, _P, _P, _P], _I32),
     "sil_render": ([_P, _I64, _I64, _I64, _P, _I64, _P], _I32),
+    "sil_unet_config_default": ([ctypes.c_void_p], _I32),
+    "sil_unet_num_layers": ([_I32], _I32),
+    "sil_unet_layer_shape": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I32)], _I32),
+    "sil_unet_flops_per_chip": ([_P], _I64),
+    "sil_unet_create": ([ctypes.POINTER(_P), _P, ctypes.POINTER(ctypes.POINTER(ctypes.c_float)),
+                         ctypes.POINTER(ctypes.POINTER(ctypes.c_float)), _I32], _I32),
+    "sil_unet_destroy": ([_P], None),
+    "sil_unet_forward": ([_P, _P, _I32, _P, _P, _P], _I32),
+    "sil_unet_error_count": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I32),
+    "sil_unet_tensor_shape": ([_P, _I32, ctypes.POINTER(_I64)], _I32),
+    "sil_unet_copy_tensor": ([_P, _I32, _P, _P], _I32),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -372,3 +383,89 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------
+# U-Net inference on filtered chips (include/sil_unet.h)
+# --------------------------------------------------------------------------
+class sil_unet_config(ctypes.Structure):
+    _fields_ = [("base_width", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32)]
+
+
+UNET_CONV3, UNET_UP, UNET_HEAD = 0, 1, 2
+
+
+def unet_config(base_width: int = 32, depth: int = 4, max_batch: int = 32) -> sil_unet_config:
+    c = sil_unet_config()
+    check(_lib.sil_unet_config_default(ctypes.byref(c)))
+    c.base_width, c.depth, c.max_batch = int(base_width), int(depth), int(max_batch)
+    return c
+
+
+def unet_layer_shapes(cfg: sil_unet_config):
+    """[(weight shape, kind)] in the library's layer order."""
+    out = []
+    for i in range(_lib.sil_unet_num_layers(cfg.depth)):
+        dims = (_I64 * 4)()
+        kind = _I32()
+        check(_lib.sil_unet_layer_shape(ctypes.byref(cfg), i, dims, ctypes.byref(kind)))
+        out.append((tuple(int(d) for d in dims), int(kind.value)))
+    return out
+
+
+class UNet:
+    """A network on the current CUDA device.  ``weights``: list of (w, b)
+    float32 numpy arrays in the library's layer order (PyTorch layouts)."""
+
+    def __init__(self, cfg: sil_unet_config, weights, device: int = 0):
+        shapes = unet_layer_shapes(cfg)
+        if len(weights) != len(shapes):
+            raise ValueError(f"{len(weights)} layers given, {len(shapes)} expected")
+        self._keep = []
+        W = (ctypes.POINTER(ctypes.c_float) * len(shapes))()
+        B = (ctypes.POINTER(ctypes.c_float) * len(shapes))()
+        for i, ((w, b), (shape, kind)) in enumerate(zip(weights, shapes)):
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            b = np.ascontiguousarray(b, dtype=np.float32)
+            if w.shape != shape:
+                raise ValueError(f"layer {i}: weight shape {w.shape}, expected {shape}")
+            self._keep += [w, b]
+            W[i] = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+            B[i] = b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        self.cfg = cfg
+        self.handle = _P()
+        check(_lib.sil_unet_create(ctypes.byref(self.handle), ctypes.byref(cfg), W, B, int(device)))
+        self._keep = None
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.sil_unet_destroy(self.handle)
+            self.handle = None
+
+    def flops_per_chip(self) -> int:
+        return int(_lib.sil_unet_flops_per_chip(ctypes.byref(self.cfg)))
+
+    def forward(self, chips, labels=None, logits=None, stream=None):
+        """chips: cuda uint8 [n, 256, 256, 3]; labels: cuda uint8 [n, 256, 256]
+        or None; logits: cuda float32 [n, 256, 256, 3] or None."""
+        n = int(chips.shape[0])
+        check(_lib.sil_unet_forward(self.handle, chips.data_ptr(), n,
+                                    labels.data_ptr() if labels is not None else None,
+                                    logits.data_ptr() if logits is not None else None,
+                                    _stream_handle(stream)))
+
+    def error_count(self) -> int:
+        v = ctypes.c_uint32()
+        check(_lib.sil_unet_error_count(self.handle, ctypes.byref(v)))
+        return int(v.value)
+
+    def tensor(self, i: int, stream=None):
+        """Copy of layer i's output activation (i = -1: the prepared input) as
+        a cuda bfloat16 tensor [n, H, W, C]."""
+        import torch
+        dims = (_I64 * 4)()
+        check(_lib.sil_unet_tensor_shape(self.handle, int(i), dims))
+        out = torch.empty(tuple(int(d) for d in dims), dtype=torch.bfloat16, device="cuda")
+        check(_lib.sil_unet_copy_tensor(self.handle, int(i), out.data_ptr(), _stream_handle(stream)))
+        return out

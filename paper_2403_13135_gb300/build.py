@@ -37,7 +37,7 @@ def _sources():
 
 def _deps():
     return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
-            + [os.path.join(INCLUDE, "sil.h"), os.path.abspath(__file__)])
+            + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:

@@ -1,0 +1,860 @@
+// sil_unet.cu -- U-Net inference on 256 x 256 chips (Sec. III-C "U-Net
+// Model Inferencing"), the 3x3 and transposed convolutions as implicit GEMMs
+// on the tcgen05 tensor cores.
+//
+// Convolution kernel (k_conv): one CTA computes a tile of 128 pixels x NT
+// output channels, D[p][n] = sum_k A[p][k] B[n][k], with
+//   3x3:  k = tap * Ci + c, A[p][k] = x[pixel p shifted by tap][c] (zero
+//         outside the image), B[n][k] = w[n][c][tap / 3][tap % 3];
+//   2x2 transposed, stride 2:  k = c, A[p][k] = x[p][c], n = (2 i + j) Co + co,
+//         B[n][k] = w[c][co][i][j]; column n of input pixel (y, x) is output
+//         pixel (2 y + i, 2 x + j), channel co.
+// Warps 0-3 gather A for 64-wide K stages with 16-byte cp.async (zero fill
+// for padding) straight into the 128-byte-swizzled K-major layout the MMA
+// reads; thread 0 also brings the stage's B block (pre-arranged on the host
+// in the same layout) with one bulk copy.  Warp 4 issues 4 MMAs
+// (128 x NT x 16, bf16 in, f32 accumulate in tensor memory) per stage.
+// Stages are handed over with mbarriers (full: 128 cp.async arrivals + the
+// bulk copy's bytes; empty: the MMA commit).  The epilogue (warps 0-3, one
+// pixel row each) reads the accumulator from tensor memory, adds the bias,
+// applies ReLU, rounds to bfloat16 and stores channels-last.  Every wait is
+// bounded; a wait that runs out counts an error and the CTA still frees its
+// tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sil.h"
+#include "sil_common.h"
+#include "sil_unet.h"
+
+namespace sil {
+namespace unet {
+
+constexpr int kChip = 256;
+constexpr int kBM = 128;           // pixels per tile (MMA M)
+constexpr int kBK = 64;            // K per stage: one 128-byte row of bf16
+constexpr int kProducers = 128;    // warps 0-3
+constexpr int kConvThreads = 160;  // + warp 4 (MMA issue)
+constexpr int kInCh = 8;           // prepared input channels (R, G, B, 5 zeros)
+constexpr int kClasses = 3;
+
+struct ConvArgs {
+  const __nv_bfloat16* x;  // input, first channel of pixel 0
+  int64_t xs;              // elements between input pixels
+  int H, W;                // input height and width
+  int cin_log2;            // log2(Ci), Ci a power of two >= 8
+  int M;                   // n H W input pixels
+  int KT;                  // K stages of 64
+  int up;                  // 0: 3x3 conv, 1: 2x2 stride-2 transposed conv
+  const uint8_t* wblk;     // [N / NT][KT] swizzled NT x 64 bf16 blocks
+  const float* bias;       // [cout]
+  int cout;                // output channels (per sub-position when up)
+  __nv_bfloat16* y;        // output, first channel of pixel 0
+  int64_t ys;              // elements between output pixels
+  int relu;
+  unsigned int* err;       // count of bounded waits that ran out
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of `parity` to complete; gives up (false) after about
+// 2^20 polls or as soon as another role of the CTA has given up.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* failed) {
+  for (int i = 0; i < (1 << 20); ++i) {
+    if (mbar_test(a, parity)) return true;
+    if (*failed) return false;
+    if (i > 32) __nanosleep(i < 4096 ? 32 : 256);
+  }
+  return false;
+}
+__device__ __forceinline__ void give_up(volatile int* failed, unsigned int* err) {
+  *failed = 1;
+  atomicAdd(err, 1u);
+}
+// 128-byte swizzle, K-major: rows of 128 bytes, 8-row atoms of 1024 bytes,
+// stride between atoms (SBO) 1024 bytes, descriptor version 1 (bit 46).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return uint64_t((addr & 0x3FFFFu) >> 4) | (uint64_t(16 >> 4) << 16) |
+         (uint64_t(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+template <int NT>
+struct ConvCfg {
+  static constexpr int kStages = NT >= 128 ? 3 : 4;
+  static constexpr int kA = kBM * kBK * 2;
+  static constexpr int kB = NT * kBK * 2;
+  static constexpr int kStage = kA + kB;
+  static constexpr int kSmem = kStages * kStage + 1024;  // + alignment slack
+  static constexpr int kTmemCols = NT < 32 ? 32 : NT;
+  // kind::f16 instruction descriptor: D f32, A and B bf16, both K-major,
+  // N >> 3 at bit 17, M >> 4 at bit 24.
+  static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                     (uint32_t(NT >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
+};
+
+template <int NT>
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv(const ConvArgs a) {
+  using C = ConvCfg<NT>;
+  constexpr int S = C::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int failed_s;
+  volatile int* failed = &failed_s;
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kBM, nt = blockIdx.y;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), kProducers + 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    failed_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(C::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const int HW = a.H * a.W;
+
+  if (warp < 4) {
+    // ---- producers: rows 32 warp + 4 i + lane / 8, 16-byte chunk lane % 8
+    const int j = lane & 7;
+    int pb[8], py[8], px[8];
+    uint32_t soff[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = 32 * warp + 4 * i + (lane >> 3);
+      const int p = m0 + r;
+      const int b = p / HW, rem = p - b * HW;
+      pb[i] = p < a.M ? b : -1;
+      py[i] = rem / a.W;
+      px[i] = rem - py[i] * a.W;
+      soff[i] = uint32_t((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
+    }
+    const int cmask = (1 << a.cin_log2) - 1;
+    for (int kt = 0; kt < a.KT; ++kt) {
+      const int s = kt % S;
+      if (kt >= S && !mbar_wait(smem_u32(&empty_bar[s]), uint32_t((kt / S - 1) & 1), failed)) {
+        give_up(failed, a.err);
+        break;
+      }
+      const uint32_t a_s = smem_u32(smem + s * C::kStage);
+      const int k = kt * kBK + 8 * j;
+      int tap, c;
+      bool tap_ok;
+      if (a.up) {
+        tap = 4;
+        c = k;
+        tap_ok = k <= cmask;
+      } else {
+        tap = k >> a.cin_log2;
+        c = k & cmask;
+        tap_ok = tap < 9;
+      }
+      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int yy = py[i] + dy, xx = px[i] + dx;
+        const bool ok = tap_ok && pb[i] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        const __nv_bfloat16* src =
+            ok ? a.x + ((int64_t(pb[i]) * a.H + yy) * a.W + xx) * a.xs + c : a.x;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(a_s + soff[i]), "l"(src),
+                     "r"(ok ? 16 : 0)
+                     : "memory");
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                       smem_u32(&full_bar[s]))
+                   : "memory");
+      if (tid == 0) {
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                     "r"(uint32_t(C::kB))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                a_s + uint32_t(C::kA)),
+            "l"(a.wblk + (size_t(nt) * a.KT + kt) * C::kB), "r"(uint32_t(C::kB)), "r"(fb)
+            : "memory");
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (lane == 0) {
+    // ---- MMA issue (warp 4, one thread)
+    bool ok = true;
+    for (int kt = 0; kt < a.KT; ++kt) {
+      const int s = kt % S;
+      if (!mbar_wait(smem_u32(&full_bar[s]), uint32_t((kt / S) & 1), failed)) {
+        give_up(failed, a.err);
+        ok = false;
+        break;
+      }
+      // the A stage was written through the generic proxy (cp.async)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(smem + s * C::kStage), b0 = a0 + uint32_t(C::kA);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint64_t ad = sw128_desc(a0 + 32 * kk), bd = sw128_desc(b0 + 32 * kk);
+        const uint32_t acc = (kt | kk) ? 1u : 0u;
+        asm volatile(
+            "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                tmem),
+            "l"(ad), "l"(bd), "r"(C::kIdesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty_bar[s]))
+                   : "memory");
+    }
+    if (ok)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&done_bar))
+                   : "memory");
+  }
+
+  if (warp < 4) {
+    // ---- epilogue: thread = pixel row, 16 columns per step
+    const bool ok = mbar_wait(smem_u32(&done_bar), 0u, failed);
+    if (!ok && tid == 0 && !*failed) give_up(failed, a.err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int r = 32 * warp + lane, p = m0 + r;
+    const int b = p / HW, rem = p - b * HW, y = rem / a.W, x = rem - (rem / a.W) * a.W;
+    if (ok) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < NT; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t ta = tmem + (uint32_t(32 * warp) << 16) + uint32_t(c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (p < a.M) {
+          const int n = nt * NT + c0;
+          int co = n;
+          int64_t opix = p;
+          if (a.up) {
+            const int sub = n / a.cout;
+            co = n - sub * a.cout;
+            opix = (int64_t(b) * 2 * a.H + 2 * y + (sub >> 1)) * (2 * a.W) + 2 * x + (sub & 1);
+          }
+          uint32_t packed[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float f0 = __uint_as_float(v[2 * q]) + a.bias[co + 2 * q];
+            float f1 = __uint_as_float(v[2 * q + 1]) + a.bias[co + 2 * q + 1];
+            if (a.relu) {
+              f0 = fmaxf(f0, 0.f);
+              f1 = fmaxf(f1, 0.f);
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+            packed[q] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(a.y + opix * a.ys + co);
+          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::kTmemCols)
+                 : "memory");
+}
+
+// R, G, B bytes -> 8 bf16 channels (v / 256, exact; channels 3..7 zero).
+__global__ void k_prep(const uint8_t* __restrict__ chips, int64_t P, __nv_bfloat16* __restrict__ x) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const uint8_t* s = chips + 3 * p;
+  const __nv_bfloat162 rg = __floats2bfloat162_rn(s[0] * (1.f / 256.f), s[1] * (1.f / 256.f));
+  const __nv_bfloat162 b0 = __floats2bfloat162_rn(s[2] * (1.f / 256.f), 0.f);
+  uint4 o;
+  o.x = *reinterpret_cast<const uint32_t*>(&rg);
+  o.y = *reinterpret_cast<const uint32_t*>(&b0);
+  o.z = 0;
+  o.w = 0;
+  reinterpret_cast<uint4*>(x)[p] = o;
+}
+
+// 2x2 max pooling; one thread per (output pixel, 8 channels).
+__global__ void k_pool(const __nv_bfloat16* __restrict__ x, int64_t xs, int H, int W, int C,
+                       int64_t n_out_px, __nv_bfloat16* __restrict__ y) {
+  const int groups = C >> 3;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_out_px * groups) return;
+  const int g = int(t % groups);
+  const int64_t q = t / groups;
+  const int Wo = W >> 1, Ho = H >> 1;
+  const int64_t b = q / (int64_t(Ho) * Wo);
+  const int rem = int(q - b * Ho * Wo), yo = rem / Wo, xo = rem - yo * Wo;
+  const int64_t p00 = (b * H + 2 * yo) * W + 2 * xo;
+  const int64_t offs[4] = {p00, p00 + 1, p00 + W, p00 + W + 1};
+  uint4 m;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint4 v = *reinterpret_cast<const uint4*>(x + offs[k] * xs + 8 * g);
+    if (k == 0) {
+      m = v;
+    } else {
+      __nv_bfloat162* mm = reinterpret_cast<__nv_bfloat162*>(&m);
+      const __nv_bfloat162* vv = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) mm[e] = __hmax2(mm[e], vv[e]);
+    }
+  }
+  *reinterpret_cast<uint4*>(y + q * C + 8 * g) = m;
+}
+
+// 1x1 head: 3 float32 scores per pixel, label = first largest.
+__global__ void k_head(const __nv_bfloat16* __restrict__ x, int F, int64_t P,
+                       const float* __restrict__ w, const float* __restrict__ bias,
+                       float* __restrict__ logits, uint8_t* __restrict__ labels) {
+  __shared__ float ws[kClasses * 64];
+  for (int i = threadIdx.x; i < kClasses * F; i += blockDim.x) ws[i] = w[i];
+  __syncthreads();
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float acc[kClasses] = {bias[0], bias[1], bias[2]};
+  for (int c0 = 0; c0 < F; c0 += 8) {
+    const uint4 v = *reinterpret_cast<const uint4*>(x + p * F + c0);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(h[e]);
+#pragma unroll
+      for (int k = 0; k < kClasses; ++k) {
+        acc[k] = __fmaf_rn(f.x, ws[k * F + c0 + 2 * e], acc[k]);
+        acc[k] = __fmaf_rn(f.y, ws[k * F + c0 + 2 * e + 1], acc[k]);
+      }
+    }
+  }
+  if (logits) {
+#pragma unroll
+    for (int k = 0; k < kClasses; ++k) logits[p * kClasses + k] = acc[k];
+  }
+  if (labels) {
+    int best = 0;
+    for (int k = 1; k < kClasses; ++k)
+      if (acc[k] > acc[best]) best = k;
+    labels[p] = uint8_t(best);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+struct Tensor {
+  __nv_bfloat16* base = nullptr;  // first channel of pixel 0
+  int64_t stride = 0;             // elements between pixels
+  int H = 0, W = 0, C = 0;
+};
+
+struct Layer {
+  int kind = 0;  // SIL_UNET_CONV3 / UP / HEAD
+  int ci = 0, co = 0, cin_pad = 0, K = 0, KT = 0, N = 0, NT = 0;
+  uint8_t* wblk = nullptr;
+  float* bias = nullptr;
+  Tensor in, out;
+  bool relu = false;
+};
+
+}  // namespace unet
+}  // namespace sil
+
+struct sil_unet {
+  int device = 0;
+  sil_unet_config cfg{};
+  std::vector<sil::unet::Layer> layers;
+  std::vector<void*> allocs;
+  __nv_bfloat16* x0 = nullptr;
+  struct Pool {
+    sil::unet::Tensor in, out;
+  };
+  std::vector<Pool> pools;
+  float* head_w = nullptr;
+  float* head_b = nullptr;
+  unsigned int* err = nullptr;
+  int last_n = 0;
+};
+
+namespace {
+
+using sil::set_error;
+using namespace sil::unet;
+
+bool config_ok(const sil_unet_config* c) {
+  return c && (c->base_width == 16 || c->base_width == 32 || c->base_width == 64) &&
+         c->depth >= 1 && c->depth <= 4 && c->max_batch >= 1 && c->max_batch <= 4096;
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+uint16_t f2bf(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest, ties to even
+  return uint16_t(u >> 16);
+}
+
+// byte offset of element (row rr, k) in an NT x 64 block, 128-byte swizzle
+size_t sw128_off(int rr, int k) {
+  return size_t(rr >> 3) * 1024 + size_t(rr & 7) * 128 + size_t(((k >> 3) ^ (rr & 7)) << 4) +
+         size_t(k & 7) * 2;
+}
+
+template <int NT>
+cudaError_t launch_conv_nt(const ConvArgs& a, int mtiles, int ntiles, cudaStream_t s) {
+  static bool attr_set = false;  // per process; set before the first launch
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               ConvCfg<NT>::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_conv<NT><<<dim3(mtiles, ntiles), kConvThreads, ConvCfg<NT>::kSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t run_layer(const Layer& L, int n, unsigned int* err, cudaStream_t s) {
+  ConvArgs a;
+  a.x = L.in.base;
+  a.xs = L.in.stride;
+  a.H = L.in.H;
+  a.W = L.in.W;
+  a.cin_log2 = ilog2(L.cin_pad);
+  a.M = n * L.in.H * L.in.W;
+  a.KT = L.KT;
+  a.up = L.kind == SIL_UNET_UP;
+  a.wblk = L.wblk;
+  a.bias = L.bias;
+  a.cout = L.co;
+  a.y = L.out.base;
+  a.ys = L.out.stride;
+  a.relu = L.relu;
+  a.err = err;
+  const int mtiles = (a.M + kBM - 1) / kBM, ntiles = L.N / L.NT;
+  switch (L.NT) {
+    case 16: return launch_conv_nt<16>(a, mtiles, ntiles, s);
+    case 32: return launch_conv_nt<32>(a, mtiles, ntiles, s);
+    case 64: return launch_conv_nt<64>(a, mtiles, ntiles, s);
+    default: return launch_conv_nt<128>(a, mtiles, ntiles, s);
+  }
+}
+
+// Weight shape (PyTorch layout) and kind of layer i; false if out of range.
+bool layer_shape(const sil_unet_config& c, int i, int64_t dims[4], int* kind) {
+  const int D = c.depth, F = c.base_width;
+  auto w = [&](int l) { return int64_t(F) << l; };
+  auto set = [&](int64_t a, int64_t b, int64_t k, int kd) {
+    dims[0] = a;
+    dims[1] = b;
+    dims[2] = k;
+    dims[3] = k;
+    *kind = kd;
+    return true;
+  };
+  if (i < 0) return false;
+  if (i < 2 * D) {
+    const int l = i / 2;
+    if (i % 2 == 0) return set(w(l), l == 0 ? 3 : w(l - 1), 3, SIL_UNET_CONV3);
+    return set(w(l), w(l), 3, SIL_UNET_CONV3);
+  }
+  i -= 2 * D;
+  if (i == 0) return set(w(D), w(D - 1), 3, SIL_UNET_CONV3);
+  if (i == 1) return set(w(D), w(D), 3, SIL_UNET_CONV3);
+  i -= 2;
+  if (i < 3 * D) {
+    const int l = D - 1 - i / 3;
+    if (i % 3 == 0) return set(w(l + 1), w(l), 2, SIL_UNET_UP);
+    if (i % 3 == 1) return set(w(l), 2 * w(l), 3, SIL_UNET_CONV3);
+    return set(w(l), w(l), 3, SIL_UNET_CONV3);
+  }
+  i -= 3 * D;
+  if (i == 0) return set(kClasses, F, 1, SIL_UNET_HEAD);
+  return false;
+}
+
+}  // namespace
+
+extern "C" sil_status sil_unet_config_default(sil_unet_config* cfg) {
+  if (!cfg) {
+    set_error("sil_unet_config_default: NULL");
+    return SIL_EINVAL;
+  }
+  cfg->base_width = 32;
+  cfg->depth = 4;
+  cfg->max_batch = 32;
+  return SIL_OK;
+}
+
+extern "C" int32_t sil_unet_num_layers(int32_t depth) {
+  return (depth >= 1 && depth <= 4) ? 5 * depth + 3 : -1;
+}
+
+extern "C" sil_status sil_unet_layer_shape(const sil_unet_config* cfg, int32_t i, int64_t dims[4],
+                                           int32_t* kind) {
+  if (!config_ok(cfg) || !dims || !kind) {
+    set_error("sil_unet_layer_shape: bad config or NULL output");
+    return SIL_EINVAL;
+  }
+  int k = 0;
+  if (!layer_shape(*cfg, i, dims, &k)) {
+    set_error("sil_unet_layer_shape: layer %d out of range", int(i));
+    return SIL_EINVAL;
+  }
+  *kind = k;
+  return SIL_OK;
+}
+
+extern "C" int64_t sil_unet_flops_per_chip(const sil_unet_config* cfg) {
+  if (!config_ok(cfg)) return -1;
+  int64_t total = 0;
+  const int nl = sil_unet_num_layers(cfg->depth);
+  for (int i = 0; i < nl; ++i) {
+    int64_t d[4];
+    int kind = 0;
+    layer_shape(*cfg, i, d, &kind);
+    // output resolution of the layer
+    int level;
+    if (i < 2 * cfg->depth) {
+      level = i / 2;
+    } else if (i < 2 * cfg->depth + 2) {
+      level = cfg->depth;
+    } else if (i < nl - 1) {
+      level = cfg->depth - 1 - (i - 2 * cfg->depth - 2) / 3;
+    } else {
+      level = 0;
+    }
+    const int64_t px = int64_t(kChip >> level) * (kChip >> level);
+    if (kind == SIL_UNET_CONV3) total += 2 * px * d[0] * d[1] * 9;
+    if (kind == SIL_UNET_UP) total += 2 * px * d[0] * d[1];  // every output px: Ci terms
+    if (kind == SIL_UNET_HEAD) total += 2 * px * d[0] * d[1];
+  }
+  return total;
+}
+
+extern "C" void sil_unet_destroy(sil_unet* net) {
+  if (!net) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(net->device);
+  for (void* p : net->allocs) cudaFree(p);
+  cudaSetDevice(prev);
+  delete net;
+}
+
+extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg,
+                                      const float* const* weights, const float* const* biases,
+                                      int32_t device) {
+  if (!out || !config_ok(cfg) || !weights || !biases) {
+    set_error("sil_unet_create: NULL argument or config outside F in {16,32,64}, depth 1..4, "
+              "max_batch 1..4096");
+    return SIL_EINVAL;
+  }
+  *out = nullptr;
+  const int nl = sil_unet_num_layers(cfg->depth);
+  for (int i = 0; i < nl; ++i)
+    if (!weights[i] || !biases[i]) {
+      set_error("sil_unet_create: NULL weight or bias of layer %d", i);
+      return SIL_EINVAL;
+    }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) {
+    set_error("sil_unet_create: cudaSetDevice(%d) failed", int(device));
+    return SIL_ECUDA;
+  }
+  sil_unet* net = new (std::nothrow) sil_unet;
+  if (!net) {
+    cudaSetDevice(prev);
+    return SIL_ENOMEM;
+  }
+  net->device = device;
+  net->cfg = *cfg;
+  const int D = cfg->depth, F = cfg->base_width, B = cfg->max_batch;
+  sil_status st = SIL_OK;
+  auto dalloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (st != SIL_OK) return nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      set_error("sil_unet_create: cudaMalloc(%zu) failed", bytes);
+      st = SIL_ENOMEM;
+      return nullptr;
+    }
+    net->allocs.push_back(p);
+    return p;
+  };
+  auto act = [&](int H, int C) {
+    Tensor t;
+    t.base = static_cast<__nv_bfloat16*>(dalloc(size_t(B) * H * H * C * 2));
+    t.stride = C;
+    t.H = t.W = H;
+    t.C = C;
+    return t;
+  };
+  auto width = [&](int l) { return F << l; };
+  // activations
+  net->x0 = static_cast<__nv_bfloat16*>(dalloc(size_t(B) * kChip * kChip * kInCh * 2));
+  std::vector<Tensor> t(D), cat(D), pool(D), d0(D), d1(D);
+  for (int l = 0; l < D; ++l) {
+    const int H = kChip >> l;
+    t[l] = act(H, width(l));
+    cat[l] = act(H, 2 * width(l));
+    pool[l] = act(H / 2, width(l));
+    d0[l] = act(H, width(l));
+    d1[l] = act(H, width(l));
+  }
+  const Tensor b0 = act(kChip >> D, width(D)), b1 = act(kChip >> D, width(D));
+  net->err = static_cast<unsigned int*>(dalloc(sizeof(unsigned int)));
+  if (st == SIL_OK && cudaMemset(net->err, 0, sizeof(unsigned int)) != cudaSuccess) st = SIL_ECUDA;
+  auto skip_of = [&](int l) {  // encoder output of level l: second half of cat[l]
+    Tensor s = cat[l];
+    s.base += width(l);
+    s.C = width(l);
+    return s;
+  };
+  auto up_of = [&](int l) {  // upsampled half of cat[l]
+    Tensor s = cat[l];
+    s.C = width(l);
+    return s;
+  };
+  Tensor x0t;
+  x0t.base = net->x0;
+  x0t.stride = kInCh;
+  x0t.H = x0t.W = kChip;
+  x0t.C = kInCh;
+  // layers
+  for (int i = 0; i < nl && st == SIL_OK; ++i) {
+    int64_t d[4];
+    int kind = 0;
+    layer_shape(*cfg, i, d, &kind);
+    Layer L;
+    L.kind = kind;
+    if (kind == SIL_UNET_HEAD) {
+      net->head_w = static_cast<float*>(dalloc(sizeof(float) * kClasses * F));
+      net->head_b = static_cast<float*>(dalloc(sizeof(float) * kClasses));
+      if (st == SIL_OK &&
+          (cudaMemcpy(net->head_w, weights[i], sizeof(float) * kClasses * F, cudaMemcpyHostToDevice) !=
+               cudaSuccess ||
+           cudaMemcpy(net->head_b, biases[i], sizeof(float) * kClasses, cudaMemcpyHostToDevice) !=
+               cudaSuccess))
+        st = SIL_ECUDA;
+      L.in = d1[0];
+      net->layers.push_back(L);
+      continue;
+    }
+    const bool up = kind == SIL_UNET_UP;
+    L.ci = int(up ? d[0] : d[1]);
+    L.co = int(up ? d[1] : d[0]);
+    L.cin_pad = L.ci < kInCh ? kInCh : L.ci;
+    L.K = up ? L.cin_pad : 9 * L.cin_pad;
+    L.KT = (L.K + kBK - 1) / kBK;
+    L.N = up ? 4 * L.co : L.co;
+    L.NT = L.N < 128 ? L.N : 128;
+    L.relu = !up;
+    // inputs and outputs
+    if (i < 2 * D) {
+      const int l = i / 2;
+      if (i % 2 == 0) {
+        L.in = l == 0 ? x0t : pool[l - 1];
+        L.out = t[l];
+      } else {
+        L.in = t[l];
+        L.out = skip_of(l);
+      }
+    } else if (i == 2 * D) {
+      L.in = pool[D - 1];
+      L.out = b0;
+    } else if (i == 2 * D + 1) {
+      L.in = b0;
+      L.out = b1;
+    } else {
+      const int q = i - 2 * D - 2, l = D - 1 - q / 3;
+      if (q % 3 == 0) {
+        L.in = l == D - 1 ? b1 : d1[l + 1];
+        L.out = up_of(l);
+      } else if (q % 3 == 1) {
+        L.in = cat[l];
+        L.out = d0[l];
+      } else {
+        L.in = d0[l];
+        L.out = d1[l];
+      }
+    }
+    // weights -> swizzled bf16 blocks [N / NT][KT][NT x 64]
+    const size_t blk = size_t(L.NT) * kBK * 2;
+    std::vector<uint8_t> h(size_t(L.N / L.NT) * L.KT * blk, 0);
+    const float* w = weights[i];
+    for (int n = 0; n < L.N; ++n) {
+      for (int k = 0; k < L.KT * kBK; ++k) {
+        float v = 0.f;
+        if (up) {
+          const int sub = n / L.co, co = n % L.co, c = k;
+          if (c < L.ci) v = w[((size_t(c) * L.co + co) * 2 + (sub >> 1)) * 2 + (sub & 1)];
+        } else {
+          const int tap = k / L.cin_pad, c = k % L.cin_pad;
+          if (tap < 9 && c < L.ci) v = w[((size_t(n) * L.ci + c) * 3 + tap / 3) * 3 + tap % 3];
+        }
+        const uint16_t bv = f2bf(v);
+        const size_t off = (size_t(n / L.NT) * L.KT + k / kBK) * blk + sw128_off(n % L.NT, k % kBK);
+        std::memcpy(&h[off], &bv, 2);
+      }
+    }
+    L.wblk = static_cast<uint8_t*>(dalloc(h.size()));
+    L.bias = static_cast<float*>(dalloc(sizeof(float) * L.co));
+    if (st == SIL_OK &&
+        (cudaMemcpy(L.wblk, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(L.bias, biases[i], sizeof(float) * L.co, cudaMemcpyHostToDevice) != cudaSuccess))
+      st = SIL_ECUDA;
+    net->layers.push_back(L);
+  }
+  for (int l = 0; l < D; ++l) net->pools.push_back({skip_of(l), pool[l]});
+  cudaSetDevice(prev);
+  if (st != SIL_OK) {
+    if (st == SIL_ECUDA) set_error("sil_unet_create: weight upload failed");
+    sil_unet_destroy(net);
+    return st;
+  }
+  *out = net;
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_forward(sil_unet* net, const uint8_t* chips, int32_t n,
+                                       uint8_t* labels, float* logits, sil_stream stream) {
+  if (!net || !chips || n < 1 || n > net->cfg.max_batch) {
+    set_error("sil_unet_forward: NULL network/chips or n=%d outside 1..max_batch", int(n));
+    return SIL_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int D = net->cfg.depth;
+  const int64_t P = int64_t(n) * kChip * kChip;
+  k_prep<<<unsigned((P + 255) / 256), 256, 0, s>>>(chips, P, net->x0);
+  cudaError_t e = cudaGetLastError();
+  const int nl = int(net->layers.size());
+  for (int i = 0; i < nl && e == cudaSuccess; ++i) {
+    const Layer& L = net->layers[i];
+    if (L.kind == SIL_UNET_HEAD) {
+      k_head<<<unsigned((P + 255) / 256), 256, 0, s>>>(L.in.base, net->cfg.base_width, P,
+                                                         net->head_w, net->head_b, logits, labels);
+      e = cudaGetLastError();
+      break;
+    }
+    e = run_layer(L, n, net->err, s);
+    // after the second conv of encoder level l: pool its output
+    if (e == cudaSuccess && i < 2 * D && i % 2 == 1) {
+      const auto& pl = net->pools[i / 2];
+      const int64_t out_px = int64_t(n) * pl.out.H * pl.out.W;
+      const int64_t threads = out_px * (pl.in.C / 8);
+      k_pool<<<unsigned((threads + 255) / 256), 256, 0, s>>>(pl.in.base, pl.in.stride, pl.in.H, pl.in.W,
+                                                             pl.in.C, out_px, pl.out.base);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) {
+    set_error("sil_unet_forward: launch failed: %s", cudaGetErrorString(e));
+    return SIL_ECUDA;
+  }
+  net->last_n = n;
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_error_count(sil_unet* net, uint32_t* count) {
+  if (!net || !count) {
+    set_error("sil_unet_error_count: NULL");
+    return SIL_EINVAL;
+  }
+  unsigned int v = 0;
+  const cudaError_t e = cudaMemcpy(&v, net->err, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_error("sil_unet_error_count: %s", cudaGetErrorString(e));
+    return SIL_ECUDA;
+  }
+  *count = v;
+  return SIL_OK;
+}
+
+namespace {
+bool tensor_of(const sil_unet* net, int i, Tensor* t) {
+  if (i == -1) {
+    t->base = net->x0;
+    t->stride = kInCh;
+    t->H = t->W = kChip;
+    t->C = kInCh;
+    return true;
+  }
+  if (i < 0 || i >= int(net->layers.size()) || net->layers[i].kind == SIL_UNET_HEAD) return false;
+  *t = net->layers[i].out;
+  return true;
+}
+}  // namespace
+
+extern "C" sil_status sil_unet_tensor_shape(const sil_unet* net, int32_t i, int64_t dims[4]) {
+  Tensor t;
+  if (!net || !dims || !tensor_of(net, i, &t)) {
+    set_error("sil_unet_tensor_shape: NULL or layer %d has no activation", int(i));
+    return SIL_EINVAL;
+  }
+  dims[0] = net->last_n;
+  dims[1] = t.H;
+  dims[2] = t.W;
+  dims[3] = t.C;
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_copy_tensor(const sil_unet* net, int32_t i, void* dst,
+                                           sil_stream stream) {
+  Tensor t;
+  if (!net || !dst || !tensor_of(net, i, &t) || net->last_n < 1) {
+    set_error("sil_unet_copy_tensor: NULL, no forward yet, or layer %d has no activation", int(i));
+    return SIL_EINVAL;
+  }
+  const size_t rows = size_t(net->last_n) * t.H * t.W;
+  const cudaError_t e = cudaMemcpy2DAsync(dst, size_t(t.C) * 2, t.base, size_t(t.stride) * 2,
+                                          size_t(t.C) * 2, rows, cudaMemcpyDeviceToDevice,
+                                          reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    set_error("sil_unet_copy_tensor: %s", cudaGetErrorString(e));
+    return SIL_ECUDA;
+  }
+  return SIL_OK;
+}

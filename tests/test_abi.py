@@ -1,4 +1,4 @@
-"""The C-ABI library: loads, exports every function include/sil.h declares,
+"""The C-ABI library: loads, exports every function include/*.h declares,
 and its host-only calls behave as documented.  No GPU needed."""
 import ctypes
 import os
@@ -18,15 +18,19 @@ def sil():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "sil.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sil_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(sil_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = _declared()
     for must in ("sil_label", "sil_label_batch", "sil_ctx_create", "sil_server_submit",
-                 "sil_params_default", "sil_status_string"):
+                 "sil_params_default", "sil_status_string", "sil_unet_create", "sil_unet_forward"):
         assert must in names
 
 
@@ -81,3 +85,38 @@ def test_null_arguments_rejected_without_gpu(sil):
     # no image -> invalid before any CUDA call
     st = sil.sil_label(None, 4, 4, 12, 0, ctypes.byref(p), None, 4, None, None, None)
     assert st == sil.SIL_EINVAL
+
+
+def test_unet_host_calls_without_gpu(sil):
+    """Layer shapes and flop count agree with the seeded generator's layer
+    table; bad configs are rejected on the host."""
+    import synth
+    for F, depth in ((16, 1), (32, 4), (64, 3)):
+        cfg = sil.unet_config(F, depth, 4)
+        got = sil.unet_layer_shapes(cfg)
+        ref = synth.unet_layer_shapes(F, depth)
+        assert [s for s, _ in got] == [s for s, _ in ref.values()]
+        kinds = {"conv3": sil.UNET_CONV3, "up": sil.UNET_UP, "head": sil.UNET_HEAD}
+        assert [k for _, k in got] == [kinds[k] for _, k in ref.values()]
+        # flops: 2 x multiply-adds over the layers at their output resolution
+        flops, lvl = 0, {}
+        for i, (name, (shape, kind)) in enumerate(ref.items()):
+            if name.startswith("enc"):
+                res = 256 >> int(name[3])
+            elif name.startswith("bott"):
+                res = 256 >> depth
+            elif name.startswith("up") or name.startswith("dec"):
+                res = 256 >> int(name[2] if name.startswith("up") else name[3])
+            else:
+                res = 256
+            taps = 9 if kind == "conv3" else 1
+            flops += 2 * res * res * shape[0] * shape[1] * taps
+        assert sil._lib.sil_unet_flops_per_chip(ctypes.byref(cfg)) == flops
+    bad = sil.sil_unet_config()
+    bad.base_width, bad.depth, bad.max_batch = 24, 4, 1
+    dims = (ctypes.c_int64 * 4)()
+    kind = ctypes.c_int32()
+    assert sil._lib.sil_unet_layer_shape(ctypes.byref(bad), 0, dims, ctypes.byref(kind)) == sil.SIL_EINVAL
+    assert sil._lib.sil_unet_num_layers(5) == -1
+    h = ctypes.c_void_p()
+    assert sil._lib.sil_unet_create(ctypes.byref(h), ctypes.byref(bad), None, None, 0) == sil.SIL_EINVAL

@@ -1,0 +1,129 @@
+"""U-Net inference on the GPU (tcgen05 implicit-GEMM convolutions) against
+the float64 oracle of oracle/unet.py on seeded chips and weights.
+
+Bounds, from the arithmetic: both sides round every stored activation to
+bfloat16 (8 significant bits); the GPU sums bf16 x bf16 products in float32,
+the oracle exactly.  So on the first convolution, whose inputs are identical
+(v / 256 is exact), an output may differ by at most one bfloat16 ulp, where
+the two sums straddle a rounding boundary.  Deeper layers see inputs that
+already differ by such ulps; the per-layer relative L2 difference stays a
+small multiple of the bf16 unit roundoff 2^-9 times the depth (bounded here
+by 3e-2).  Labels are compared where the oracle's best score beats the second
+by more than the logits' absolute difference bound; elsewhere either label is
+a correct argmax of scores within rounding."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import oracle.unet as U  # noqa: E402
+import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sil():
+    import paper_2403_13135_gb300 as m
+    return m
+
+
+def _chips(n, seed):
+    img, _ = synth.scene(1024, 1024, seed, n_floes=12, n_haze=2, n_shadow=2)
+    return synth.chips_from_scene(img, n, seed)
+
+
+def _oracle_chain(chips, wts, depth):
+    """Every layer's output activation of the oracle, in the library's order."""
+    x = U.prep(chips)
+    outs, skips = [], []
+    for lvl in range(depth):
+        x = U.conv3x3(x, *wts[f"enc{lvl}_0"]); outs.append(x)
+        x = U.conv3x3(x, *wts[f"enc{lvl}_1"]); outs.append(x)
+        skips.append(x)
+        x = U.maxpool2(x)
+    x = U.conv3x3(x, *wts["bott_0"]); outs.append(x)
+    x = U.conv3x3(x, *wts["bott_1"]); outs.append(x)
+    for lvl in reversed(range(depth)):
+        x = U.upconv2(x, *wts[f"up{lvl}"]); outs.append(x)
+        x = np.concatenate([x, skips[lvl]], axis=-1)
+        x = U.conv3x3(x, *wts[f"dec{lvl}_0"]); outs.append(x)
+        x = U.conv3x3(x, *wts[f"dec{lvl}_1"]); outs.append(x)
+    logits, labels = U.head(x, *wts["head"])
+    return outs, logits, labels
+
+
+def _run(sil, F, depth, chips, wts, max_batch=None):
+    cfg = sil.unet_config(F, depth, max_batch or len(chips))
+    net = sil.UNet(cfg, list(wts.values()))
+    dev = torch.from_numpy(chips).cuda()
+    lab = torch.empty(chips.shape[:3], dtype=torch.uint8, device="cuda")
+    lg = torch.empty(chips.shape[:3] + (3,), dtype=torch.float32, device="cuda")
+    net.forward(dev, lab, lg)
+    torch.cuda.synchronize()
+    return net, lab.cpu().numpy(), lg.cpu().numpy()
+
+
+def _ulp_bf16(v):
+    m, e = np.frexp(np.abs(v))
+    return np.ldexp(1.0, e - 8)
+
+
+@pytest.mark.parametrize("F,depth", [(16, 2), (32, 4)])
+def test_unet_layers_against_oracle(sil, F, depth):
+    chips = _chips(2, 11 + F)
+    wts = synth.unet_weights(F, depth, seed=F)
+    net, lab, lg = _run(sil, F, depth, chips, wts)
+    outs, ref_lg, ref_lab = _oracle_chain(chips, wts, depth)
+    # prepared input: exact
+    x0 = net.tensor(-1).float().cpu().numpy()
+    assert np.array_equal(x0[..., :3], U.prep(chips)) and not x0[..., 3:].any()
+    # first convolution: identical inputs -> at most one bf16 ulp apart
+    g0 = net.tensor(0).float().cpu().numpy().astype(np.float64)
+    d0 = np.abs(g0 - outs[0])
+    assert np.all(d0 <= _ulp_bf16(outs[0]) + 1e-30), d0.max()
+    assert np.mean(d0 == 0) > 0.95
+    # every layer: relative L2 difference
+    for i, ref in enumerate(outs):
+        g = net.tensor(i).float().cpu().numpy().astype(np.float64)
+        assert g.shape == ref.shape, (i, g.shape, ref.shape)
+        rel = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30)
+        assert rel < 3e-2, (i, rel)
+    # scores and labels
+    rel = np.linalg.norm(lg - ref_lg) / np.linalg.norm(ref_lg)
+    assert rel < 3e-2, rel
+    bound = np.abs(lg - ref_lg).max()
+    srt = np.sort(ref_lg, axis=-1)
+    clear = (srt[..., -1] - srt[..., -2]) > 2 * bound
+    assert clear.mean() > 0.5
+    assert np.array_equal(lab[clear], ref_lab[clear])
+    assert net.error_count() == 0
+
+
+def test_unet_batch_independent(sil):
+    """A chip's scores do not depend on the batch it is in (bit-exact)."""
+    F, depth = 16, 3
+    chips = _chips(5, 3)
+    wts = synth.unet_weights(F, depth, seed=7)
+    net5, lab5, lg5 = _run(sil, F, depth, chips, wts)
+    net1, lab1, lg1 = _run(sil, F, depth, chips[2:3], wts, max_batch=8)
+    assert np.array_equal(lg5[2:3], lg1) and np.array_equal(lab5[2:3], lab1)
+    assert net5.error_count() == 0 and net1.error_count() == 0
+
+
+def test_unet_rejects_bad_arguments(sil):
+    cfg = sil.unet_config(32, 4, 2)
+    wts = list(synth.unet_weights(32, 4, 0).values())
+    net = sil.UNet(cfg, wts)
+    dev = torch.zeros((3, 256, 256, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(sil.SilError):
+        net.forward(dev)                 # 3 > max_batch
+    with pytest.raises(sil.SilError):
+        sil.UNet(sil.unet_config(24, 4, 2), wts)  # width not in {16, 32, 64}
+    with pytest.raises(ValueError):
+        sil.UNet(cfg, wts[:-1])
