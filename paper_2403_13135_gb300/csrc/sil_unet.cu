@@ -2,8 +2,8 @@
 // Model Inferencing"), the 3x3 and transposed convolutions as implicit GEMMs
 // on the tcgen05 tensor cores.
 //
-// Convolution kernel (k_conv): one CTA computes a tile of 128 pixels x NT
-// output channels, D[p][n] = sum_k A[p][k] B[n][k], with
+// Convolution kernel (k_conv): a tile is 128 pixels x NT output channels,
+// D[p][n] = sum_k A[p][k] B[n][k], with
 //   3x3:  k = tap * Ci + c, A[p][k] = x[pixel p shifted by tap][c] (zero
 //         outside the image), B[n][k] = w[n][c][tap / 3][tap % 3];
 //   2x2 transposed, stride 2:  k = c, A[p][k] = x[p][c], n = (2 i + j) Co + co,
@@ -12,14 +12,15 @@
 // Warps 0-3 gather A for 64-wide K stages with 16-byte cp.async (zero fill
 // for padding) straight into the 128-byte-swizzled K-major layout the MMA
 // reads; thread 0 also brings the stage's B block (pre-arranged on the host
-// in the same layout) with one bulk copy.  Warp 4 issues 4 MMAs
+// in the same layout) with one bulk copy.  Warp 8 issues 4 MMAs
 // (128 x NT x 16, bf16 in, f32 accumulate in tensor memory) per stage.
 // Stages are handed over with mbarriers (full: 128 cp.async arrivals + the
-// bulk copy's bytes; empty: the MMA commit).  The epilogue (warps 0-3, one
-// pixel row each) reads the accumulator from tensor memory, adds the bias,
-// applies ReLU, rounds to bfloat16 and stores channels-last.  Every wait is
-// bounded; a wait that runs out counts an error and the CTA still frees its
-// tensor memory.
+// bulk copy's bytes; empty: the MMA commit).  CTAs are persistent over the
+// tiles and keep two accumulators in tensor memory: while warp 8 fills one,
+// the epilogue (warps 4-7, one pixel row per thread) reads the other, adds
+// the bias, applies ReLU, rounds to bfloat16 and stores channels-last.
+// Every wait is bounded; a wait that runs out counts an error and the CTA
+// still frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -39,8 +40,9 @@ namespace unet {
 constexpr int kChip = 256;
 constexpr int kBM = 128;           // pixels per tile (MMA M)
 constexpr int kBK = 64;            // K per stage: one 128-byte row of bf16
-constexpr int kProducers = 128;    // warps 0-3
-constexpr int kConvThreads = 160;  // + warp 4 (MMA issue)
+constexpr int kProducers = 128;    // warps 0-3: A and B stages
+constexpr int kEpilogue = 128;     // warps 4-7: accumulator -> bf16 output
+constexpr int kConvThreads = 288;  // + warp 8: MMA issue
 constexpr int kInCh = 8;           // prepared input channels (R, G, B, 5 zeros)
 constexpr int kClasses = 3;
 
@@ -104,32 +106,39 @@ struct ConvCfg {
   static constexpr int kB = NT * kBK * 2;
   static constexpr int kStage = kA + kB;
   static constexpr int kSmem = kStages * kStage + 1024;  // + alignment slack
-  static constexpr int kTmemCols = NT < 32 ? 32 : NT;
+  // two accumulators of NT float32 columns (the epilogue of one tile runs
+  // while the next tile accumulates)
+  static constexpr int kTmemCols = 2 * NT < 32 ? 32 : 2 * NT;
   // kind::f16 instruction descriptor: D f32, A and B bf16, both K-major,
   // N >> 3 at bit 17, M >> 4 at bit 24.
   static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                      (uint32_t(NT >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
 };
 
+// Persistent: CTA b handles tiles b, b + gridDim.x, ... (tile t = M tile
+// t / ntiles, N tile t % ntiles).  Warps 0-3 produce A/B stages, warps 4-7
+// drain the accumulators, warp 8 issues the MMAs.
 template <int NT>
-__global__ void __launch_bounds__(kConvThreads, 1) k_conv(const ConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int ntiles, int ntotal) {
   using C = ConvCfg<NT>;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int failed_s;
   volatile int* failed = &failed_s;
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kBM, nt = blockIdx.y;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&full_bar[s]), kProducers + 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    mbar_init(smem_u32(&done_bar), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), kEpilogue);
+    }
     failed_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -149,111 +158,97 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const ConvArgs a) {
   if (warp < 4) {
     // ---- producers: rows 32 warp + 4 i + lane / 8, 16-byte chunk lane % 8
     const int j = lane & 7;
-    int pb[8], py[8], px[8];
     uint32_t soff[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = 32 * warp + 4 * i + (lane >> 3);
-      const int p = m0 + r;
-      const int b = p / HW, rem = p - b * HW;
-      pb[i] = p < a.M ? b : -1;
-      py[i] = rem / a.W;
-      px[i] = rem - py[i] * a.W;
       soff[i] = uint32_t((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
     }
     const int cmask = (1 << a.cin_log2) - 1;
-    for (int kt = 0; kt < a.KT; ++kt) {
-      const int s = kt % S;
-      if (kt >= S && !mbar_wait(smem_u32(&empty_bar[s]), uint32_t((kt / S - 1) & 1), failed)) {
-        give_up(failed, a.err);
-        break;
-      }
-      const uint32_t a_s = smem_u32(smem + s * C::kStage);
-      const int k = kt * kBK + 8 * j;
-      int tap, c;
-      bool tap_ok;
-      if (a.up) {
-        tap = 4;
-        c = k;
-        tap_ok = k <= cmask;
-      } else {
-        tap = k >> a.cin_log2;
-        c = k & cmask;
-        tap_ok = tap < 9;
-      }
-      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntotal && ok; t += gridDim.x) {
+      const int mt = t / ntiles, nt = t - mt * ntiles;
+      int pb[8], py[8], px[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int yy = py[i] + dy, xx = px[i] + dx;
-        const bool ok = tap_ok && pb[i] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-        const __nv_bfloat16* src =
-            ok ? a.x + ((int64_t(pb[i]) * a.H + yy) * a.W + xx) * a.xs + c : a.x;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(a_s + soff[i]), "l"(src),
-                     "r"(ok ? 16 : 0)
-                     : "memory");
+        const int p = mt * kBM + 32 * warp + 4 * i + (lane >> 3);
+        const int b = p / HW, rem = p - b * HW;
+        pb[i] = p < a.M ? b : -1;
+        py[i] = rem / a.W;
+        px[i] = rem - py[i] * a.W;
       }
-      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
-                       smem_u32(&full_bar[s]))
-                   : "memory");
-      if (tid == 0) {
-        const uint32_t fb = smem_u32(&full_bar[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                     "r"(uint32_t(C::kB))
+      for (int kt = 0; kt < a.KT; ++kt, ++it) {
+        const int s = it % S;
+        if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), uint32_t((it / S - 1) & 1), failed)) {
+          give_up(failed, a.err);
+          ok = false;
+          break;
+        }
+        const uint32_t a_s = smem_u32(smem + s * C::kStage);
+        const int k = kt * kBK + 8 * j;
+        int tap, c;
+        bool tap_ok;
+        if (a.up) {
+          tap = 4;
+          c = k;
+          tap_ok = k <= cmask;
+        } else {
+          tap = k >> a.cin_log2;
+          c = k & cmask;
+          tap_ok = tap < 9;
+        }
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int yy = py[i] + dy, xx = px[i] + dx;
+          const bool in = tap_ok && pb[i] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+          const __nv_bfloat16* src =
+              in ? a.x + ((int64_t(pb[i]) * a.H + yy) * a.W + xx) * a.xs + c : a.x;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(a_s + soff[i]),
+                       "l"(src), "r"(in ? 16 : 0)
+                       : "memory");
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                         smem_u32(&full_bar[s]))
                      : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                a_s + uint32_t(C::kA)),
-            "l"(a.wblk + (size_t(nt) * a.KT + kt) * C::kB), "r"(uint32_t(C::kB)), "r"(fb)
-            : "memory");
+        if (tid == 0) {
+          const uint32_t fb = smem_u32(&full_bar[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                       "r"(uint32_t(C::kB))
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  a_s + uint32_t(C::kA)),
+              "l"(a.wblk + (size_t(nt) * a.KT + kt) * C::kB), "r"(uint32_t(C::kB)), "r"(fb)
+              : "memory");
+        }
       }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-  } else if (lane == 0) {
-    // ---- MMA issue (warp 4, one thread)
-    bool ok = true;
-    for (int kt = 0; kt < a.KT; ++kt) {
-      const int s = kt % S;
-      if (!mbar_wait(smem_u32(&full_bar[s]), uint32_t((kt / S) & 1), failed)) {
+    // tail: the MMA commits of the last stages arrive before the CTA ends
+    for (int i = it - S; ok && i < it; ++i)
+      if (i >= 0 && !mbar_wait(smem_u32(&empty_bar[i % S]), uint32_t((i / S) & 1), failed)) {
         give_up(failed, a.err);
         ok = false;
+      }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp < 8) {
+    // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31
+    const int q = warp & 3, r = 32 * q + lane;
+    int tl = 0;
+    for (int t = blockIdx.x; t < ntotal; t += gridDim.x, ++tl) {
+      const int mt = t / ntiles, nt = t - mt * ntiles, buf = tl & 1;
+      if (!mbar_wait(smem_u32(&acc_full[buf]), uint32_t((tl >> 1) & 1), failed)) {
+        if (lane == 0) give_up(failed, a.err);
         break;
       }
-      // the A stage was written through the generic proxy (cp.async)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(smem + s * C::kStage), b0 = a0 + uint32_t(C::kA);
-#pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        const uint64_t ad = sw128_desc(a0 + 32 * kk), bd = sw128_desc(b0 + 32 * kk);
-        const uint32_t acc = (kt | kk) ? 1u : 0u;
-        asm volatile(
-            "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
-                tmem),
-            "l"(ad), "l"(bd), "r"(C::kIdesc), "r"(acc)
-            : "memory");
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&empty_bar[s]))
-                   : "memory");
-    }
-    if (ok)
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&done_bar))
-                   : "memory");
-  }
-
-  if (warp < 4) {
-    // ---- epilogue: thread = pixel row, 16 columns per step
-    const bool ok = mbar_wait(smem_u32(&done_bar), 0u, failed);
-    if (!ok && tid == 0 && !*failed) give_up(failed, a.err);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int r = 32 * warp + lane, p = m0 + r;
-    const int b = p / HW, rem = p - b * HW, y = rem / a.W, x = rem - (rem / a.W) * a.W;
-    if (ok) {
+      const int p = mt * kBM + r;
+      const int b = p / HW, rem = p - b * HW, y = rem / a.W, x = rem - (rem / a.W) * a.W;
 #pragma unroll 1
       for (int c0 = 0; c0 < NT; c0 += 16) {
         uint32_t v[16];
-        const uint32_t ta = tmem + (uint32_t(32 * warp) << 16) + uint32_t(c0);
+        const uint32_t ta = tmem + (uint32_t(32 * q) << 16) + uint32_t(buf * NT + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
@@ -272,21 +267,66 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const ConvArgs a) {
           }
           uint32_t packed[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float f0 = __uint_as_float(v[2 * q]) + a.bias[co + 2 * q];
-            float f1 = __uint_as_float(v[2 * q + 1]) + a.bias[co + 2 * q + 1];
+          for (int e = 0; e < 8; ++e) {
+            float f0 = __uint_as_float(v[2 * e]) + a.bias[co + 2 * e];
+            float f1 = __uint_as_float(v[2 * e + 1]) + a.bias[co + 2 * e + 1];
             if (a.relu) {
               f0 = fmaxf(f0, 0.f);
               f1 = fmaxf(f1, 0.f);
             }
             const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
-            packed[q] = *reinterpret_cast<const uint32_t*>(&h);
+            packed[e] = *reinterpret_cast<const uint32_t*>(&h);
           }
           uint4* dst = reinterpret_cast<uint4*>(a.y + opix * a.ys + co);
           dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
           dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
         }
       }
+      // this accumulator may be overwritten by the tile after next
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
+    }
+  } else if (lane == 0) {
+    // ---- MMA issue (warp 8, one thread)
+    int it = 0, tl = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntotal && ok; t += gridDim.x, ++tl) {
+      const int buf = tl & 1;
+      if (tl >= 2 && !mbar_wait(smem_u32(&acc_empty[buf]), uint32_t(((tl >> 1) - 1) & 1), failed)) {
+        give_up(failed, a.err);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d = tmem + uint32_t(buf * NT);
+      for (int kt = 0; kt < a.KT; ++kt, ++it) {
+        const int s = it % S;
+        if (!mbar_wait(smem_u32(&full_bar[s]), uint32_t((it / S) & 1), failed)) {
+          give_up(failed, a.err);
+          ok = false;
+          break;
+        }
+        // the A stage was written through the generic proxy (cp.async)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(smem + s * C::kStage), b0 = a0 + uint32_t(C::kA);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+          const uint64_t ad = sw128_desc(a0 + 32 * kk), bd = sw128_desc(b0 + 32 * kk);
+          const uint32_t acc = (kt | kk) ? 1u : 0u;
+          asm volatile(
+              "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                  d),
+              "l"(ad), "l"(bd), "r"(C::kIdesc), "r"(acc)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&empty_bar[s]))
+                     : "memory");
+      }
+      if (ok)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&acc_full[buf]))
+                     : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -444,14 +484,36 @@ size_t sw128_off(int rr, int k) {
 
 template <int NT>
 cudaError_t launch_conv_nt(const ConvArgs& a, int mtiles, int ntiles, cudaStream_t s) {
-  static bool attr_set = false;  // per process; set before the first launch
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               ConvCfg<NT>::kSmem);
+  static int ctas_per_sm = 0;  // per process; set before the first launch
+  static int sms = 0;
+  if (!ctas_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         ConvCfg<NT>::kSmem);
+    int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conv<NT>);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    // The occupancy calculator reports one CTA per SM for any kernel that
+    // allocates tensor memory, so the resident count is derived from the
+    // kernel's own shared memory, registers and tensor-memory columns (an
+    // SM has 512); extra CTAs of a persistent grid only start later.
+    const int by_smem = smem_sm / (ConvCfg<NT>::kSmem + int(fa.sharedSizeBytes) + reserved);
+    const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_sm / (warp_regs * (kConvThreads / 32));
+    const int by_tmem = 512 / ConvCfg<NT>::kTmemCols;
+    int c = by_smem < by_regs ? by_smem : by_regs;
+    c = c < by_tmem ? c : by_tmem;
+    ctas_per_sm = c > 0 ? c : 1;
   }
-  k_conv<NT><<<dim3(mtiles, ntiles), kConvThreads, ConvCfg<NT>::kSmem, s>>>(a);
+  const int ntotal = mtiles * ntiles;
+  const int cap = sms * ctas_per_sm;
+  const int grid = ntotal < cap ? ntotal : cap;
+  k_conv<NT><<<grid, kConvThreads, ConvCfg<NT>::kSmem, s>>>(a, ntiles, ntotal);
   return cudaGetLastError();
 }
 
