@@ -45,6 +45,7 @@ constexpr int kEpilogue = 128;     // warps 4-7: accumulator -> bf16 output
 constexpr int kConvThreads = 288;  // + warp 8: MMA issue
 constexpr int kInCh = 8;           // prepared input channels (R, G, B, 5 zeros)
 constexpr int kClasses = 3;
+constexpr int kMaxCout = 1024;     // widest layer: F = 64 at depth 4
 
 struct ConvArgs {
   const __nv_bfloat16* x;  // input, first channel of pixel 0
@@ -78,13 +79,25 @@ __device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of `parity` to complete; gives up (false) after about
-// 2^20 polls or as soon as another role of the CTA has given up.
+// One try that may suspend the thread for up to `ns` nanoseconds until the
+// phase completes (woken as soon as it does).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t a, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(a), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of `parity` to complete; gives up (false) after 2^16
+// tries of at most 20 us each (about 1.3 s) or soon after another role of
+// the CTA has given up.
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* failed) {
-  for (int i = 0; i < (1 << 20); ++i) {
-    if (mbar_test(a, parity)) return true;
-    if (*failed) return false;
-    if (i > 32) __nanosleep(i < 4096 ? 32 : 256);
+  if (mbar_test(a, parity)) return true;
+  for (int i = 0; i < (1 << 16); ++i) {
+    if (mbar_test_wait(a, parity, 20000u)) return true;
+    if ((i & 15) == 15 && *failed) return false;
   }
   return false;
 }
@@ -126,10 +139,12 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
   __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int failed_s;
+  __shared__ float bias_s[kMaxCout];
   volatile int* failed = &failed_s;
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+  for (int i = tid; i < a.cout; i += kConvThreads) bias_s[i] = a.bias[i];
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&full_bar[s]), kProducers + 1);
@@ -169,14 +184,18 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
     bool ok = true;
     for (int t = blockIdx.x; t < ntotal && ok; t += gridDim.x) {
       const int mt = t / ntiles, nt = t - mt * ntiles;
-      int pb[8], py[8], px[8];
+      // per row: element offset of its pixel and which neighbours exist
+      // (bit 0 above, 1 below, 2 left, 3 right, 4 the pixel itself)
+      int64_t pbase[8];
+      uint32_t pfl[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int p = mt * kBM + 32 * warp + 4 * i + (lane >> 3);
-        const int b = p / HW, rem = p - b * HW;
-        pb[i] = p < a.M ? b : -1;
-        py[i] = rem / a.W;
-        px[i] = rem - py[i] * a.W;
+        const int b = p / HW, rem = p - b * HW, y = rem / a.W, x = rem - y * a.W;
+        pbase[i] = ((int64_t(b) * a.H + y) * a.W + x) * a.xs;
+        pfl[i] = p < a.M ? (16u | (y > 0 ? 1u : 0u) | (y < a.H - 1 ? 2u : 0u) |
+                            (x > 0 ? 4u : 0u) | (x < a.W - 1 ? 8u : 0u))
+                         : 0u;
       }
       for (int kt = 0; kt < a.KT; ++kt, ++it) {
         const int s = it % S;
@@ -198,13 +217,14 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
           c = k & cmask;
           tap_ok = tap < 9;
         }
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+          const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const uint32_t need = 16u | (dy < 0 ? 1u : 0u) | (dy > 0 ? 2u : 0u) | (dx < 0 ? 4u : 0u) |
+                              (dx > 0 ? 8u : 0u);
+        const int64_t toff = (int64_t(dy) * a.W + dx) * a.xs + c;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int yy = py[i] + dy, xx = px[i] + dx;
-          const bool in = tap_ok && pb[i] >= 0 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-          const __nv_bfloat16* src =
-              in ? a.x + ((int64_t(pb[i]) * a.H + yy) * a.W + xx) * a.xs + c : a.x;
+          const bool in = tap_ok && (pfl[i] & need) == need;
+          const __nv_bfloat16* src = in ? a.x + (pbase[i] + toff) : a.x;
           asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(a_s + soff[i]),
                        "l"(src), "r"(in ? 16 : 0)
                        : "memory");
@@ -268,8 +288,8 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
           uint32_t packed[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            float f0 = __uint_as_float(v[2 * e]) + a.bias[co + 2 * e];
-            float f1 = __uint_as_float(v[2 * e + 1]) + a.bias[co + 2 * e + 1];
+            float f0 = __uint_as_float(v[2 * e]) + bias_s[co + 2 * e];
+            float f1 = __uint_as_float(v[2 * e + 1]) + bias_s[co + 2 * e + 1];
             if (a.relu) {
               f0 = fmaxf(f0, 0.f);
               f1 = fmaxf(f1, 0.f);
