@@ -612,6 +612,90 @@ def run_sweep(args):
     return 0
 
 
+def run_unet(args):
+    """U-Net inference on 256 x 256 chips of the scene (random weights, throughput
+    only): device-resident forward passes of a batch of chips, tensor-core
+    roofline, end to end with the chips copied in and the labels copied out."""
+    import torch
+    import paper_2403_13135_gb300 as sil
+    import synth
+    F, D, B = args.unet_width, args.unet_depth, args.unet_batch
+    img, _ = synth.full_scene(1, SIDE)
+    chips_h = synth.chips_from_scene(img, B, seed=3)
+    del img
+    wts = synth.unet_weights(F, D, seed=0)
+    net = sil.UNet(sil.unet_config(F, D, B), list(wts.values()))
+    chips = torch.from_numpy(chips_h).cuda()
+    lab = torch.empty((B, 256, 256), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup if args.warmup < 50 else 5)):
+        net.forward(chips, lab)
+    torch.cuda.synchronize()
+    steps = args.unet_steps
+    clk = ClockSampler(0)
+    clk.start()
+    time.sleep(0.15)
+    t0 = time.monotonic()
+    dt = _time_cuda(lambda: net.forward(chips, lab, stream=st), steps, st)
+    t1 = time.monotonic()
+    clk.mark(t0, t1)
+    time.sleep(0.1)
+    clk.stop()
+    flops = net.flops_per_chip() * B
+    achieved = flops / dt / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        peak, peak_src = float(pk["bf16_tflops_sustained"]), "measured bf16_tflops_sustained"
+        burst = float(pk["bf16_tflops"])
+    except Exception:
+        peak, peak_src, burst = 1700.0, "fallback (sustained)", 1900.0
+    # end to end: pinned chips in, forward, labels out, every step
+    host = torch.from_numpy(chips_h).pin_memory()
+    hl = torch.empty((B, 256, 256), dtype=torch.uint8).pin_memory()
+    e2e_steps = max(3, min(args.e2e_steps, steps))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        chips.copy_(host, non_blocking=True)
+        net.forward(chips, lab)
+        hl.copy_(lab, non_blocking=True)
+    torch.cuda.synchronize()
+    te = (time.perf_counter() - te0) / e2e_steps
+    errors = net.error_count()
+    line = {
+        "metric": "U-Net chips/s (F=%d, depth %d, bf16 tensor cores)" % (F, D),
+        "value": B / dt, "unit": "chips/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(3, args.warmup if args.warmup < 50 else 5), "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic chips of the seeded scene, seeded random weights",
+        "config": {"workload": f"U-Net inference, {B} chips of 256x256 per step, base width {F}, "
+                               f"depth {D}", "l2": "activations (~1 GB per step) larger than L2",
+                   "gpx_per_s": B * 65536 / dt / 1e9},
+        "e2e": {"value": B / te, "unit": "chips/s", "h2d_bytes_per_step": int(chips_h.nbytes),
+                "d2h_bytes_per_step": int(B * 65536)},
+        "gpu_launches": int(steps * (1 + sil._lib.sil_unet_num_layers(D) - 1)),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "frac_of_burst": achieved / burst, "flops_per_step": flops},
+        "clocks": clk.summary(),
+        "wait_errors": errors,
+    }
+    if not args.no_cpu_baseline:
+        import oracle.unet as U
+        n, t_c = 0, time.perf_counter()
+        while True:
+            U.forward(chips_h[n % B:n % B + 1], wts, depth=D)
+            n += 1
+            if time.perf_counter() - t_c > args.cpu_budget / 2:
+                break
+        tc = time.perf_counter() - t_c
+        line["cpu_baseline"] = {"value": n / tc, "unit": "chips/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n} chips through the float64 numpy oracle in {tc:.1f} s"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -626,8 +710,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0,
                     help="oracle worker processes for the CPU baseline (0 = every host core)")
-    ap.add_argument("--config", default="scene", choices=["scene", "batch", "served", "sweep"],
-                    help="scene: the headline line; batch/served/sweep: the other workloads")
+    ap.add_argument("--config", default="scene", choices=["scene", "batch", "served", "sweep", "unet"],
+                    help="scene: the headline line; batch/served/sweep/unet: the other workloads")
+    ap.add_argument("--unet-width", type=int, default=32)
+    ap.add_argument("--unet-depth", type=int, default=4)
+    ap.add_argument("--unet-batch", type=int, default=64)
+    ap.add_argument("--unet-steps", type=int, default=50)
     ap.add_argument("--tiles", type=int, default=512)
     ap.add_argument("--rates", default="50,200,1000,2000")
     ap.add_argument("--served-seconds", type=float, default=10.0)
@@ -643,6 +731,8 @@ def main():
         return run_served(args)
     if args.config == "sweep":
         return run_sweep(args)
+    if args.config == "unet":
+        return run_unet(args)
     return run_sil(args)
 
 

@@ -97,10 +97,11 @@ sil_status sil_unet_forward(sil_unet* net, const uint8_t* chips, int32_t n, uint
  * out since the network was created (0 in normal operation). */
 sil_status sil_unet_error_count(sil_unet* net, uint32_t* count);
 
-/* Output activation of layer i (sil_unet_layer_shape order; i = -1: the
- * prepared input, 8 channels of which the last 5 are zero) of the last
- * forward pass: dims = {n, H, W, C} (n of that pass).  The head (the last
- * layer) keeps no activation: SIL_EINVAL. */
+/* Output activation of layer i (sil_unet_layer_shape order) of the last
+ * forward pass: dims = {n, H, W, C} (n of that pass).  i = -1: the prepared
+ * input, 8 channels (R, G, B scaled by 1/256, then 5 zeros).  The head (the
+ * last layer) is computed inside the last decoder convolution and keeps no
+ * activation: SIL_EINVAL. */
 sil_status sil_unet_tensor_shape(const sil_unet* net, int32_t i, int64_t dims[4]);
 
 /* Copies that activation into DEVICE bfloat16 `dst`, dense [n][H][W][C]

@@ -54,15 +54,33 @@ struct ConvArgs {
   int cin_log2;            // log2(Ci), Ci a power of two >= 8
   int M;                   // n H W input pixels
   int KT;                  // K stages of 64
-  int up;                  // 0: 3x3 conv, 1: 2x2 stride-2 transposed conv
+  int up;                  // 0: conv, 1: 2x2 stride-2 transposed conv
+  int taps;                // 9: 3x3 window (k = tap Ci + c), 1: k = c
   const uint8_t* wblk;     // [N / NT][KT] swizzled NT x 64 bf16 blocks
   const float* bias;       // [cout]
   int cout;                // output channels (per sub-position when up)
   __nv_bfloat16* y;        // output, first channel of pixel 0
   int64_t ys;              // elements between output pixels
   int relu;
+  __nv_bfloat16* pool_y;   // optional 2x2 max pool of the output, [n][H/2][W/2][cout]
+  const float* head_w;     // optional fused 1x1 head ([3][cout] float32) ...
+  const float* head_b;     // ... and its bias; needs NT == cout
+  float* logits;           // head scores [n][H][W][3] (nullable)
+  uint8_t* labels;         // head argmax [n][H][W] (nullable)
   unsigned int* err;       // count of bounded waits that ran out
 };
+
+// Tiles walk the pixels in 2x2 blocks: tile index p (0 .. n H W - 1) is
+// pixel (2 Y + s / 2, 2 X + s % 2) of block q = p / 4 = (b, Y, X) row-major,
+// s = p % 4.  A 2x2 pooling window is then 4 adjacent rows of a tile (4
+// adjacent lanes of an epilogue warp), and the pooled pixel's index is q.
+__device__ __forceinline__ void tile_pixel(int p, int H, int W, int& b, int& y, int& x) {
+  const int q = p >> 2, s = p & 3, Wb = W >> 1, HWb = (H >> 1) * Wb;
+  b = q / HWb;
+  const int rem = q - b * HWb, Y = rem / Wb, X = rem - Y * Wb;
+  y = 2 * Y + (s >> 1);
+  x = 2 * X + (s & 1);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -140,11 +158,15 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
   __shared__ uint32_t tmem_slot;
   __shared__ int failed_s;
   __shared__ float bias_s[kMaxCout];
+  __shared__ float head_s[kClasses * 64 + kClasses];
   volatile int* failed = &failed_s;
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   for (int i = tid; i < a.cout; i += kConvThreads) bias_s[i] = a.bias[i];
+  if (a.head_w)
+    for (int i = tid; i < kClasses * (a.cout + 1); i += kConvThreads)
+      head_s[i] = i < kClasses * a.cout ? a.head_w[i] : a.head_b[i - kClasses * a.cout];
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&full_bar[s]), kProducers + 1);
@@ -168,8 +190,6 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const int HW = a.H * a.W;
-
   if (warp < 4) {
     // ---- producers: rows 32 warp + 4 i + lane / 8, 16-byte chunk lane % 8
     const int j = lane & 7;
@@ -191,7 +211,8 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int p = mt * kBM + 32 * warp + 4 * i + (lane >> 3);
-        const int b = p / HW, rem = p - b * HW, y = rem / a.W, x = rem - y * a.W;
+        int b, y, x;
+        tile_pixel(p, a.H, a.W, b, y, x);
         pbase[i] = ((int64_t(b) * a.H + y) * a.W + x) * a.xs;
         pfl[i] = p < a.M ? (16u | (y > 0 ? 1u : 0u) | (y < a.H - 1 ? 2u : 0u) |
                             (x > 0 ? 4u : 0u) | (x < a.W - 1 ? 8u : 0u))
@@ -208,7 +229,7 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
         const int k = kt * kBK + 8 * j;
         int tap, c;
         bool tap_ok;
-        if (a.up) {
+        if (a.taps == 1) {
           tap = 4;
           c = k;
           tap_ok = k <= cmask;
@@ -264,7 +285,12 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int p = mt * kBM + r;
-      const int b = p / HW, rem = p - b * HW, y = rem / a.W, x = rem - (rem / a.W) * a.W;
+      int b, y, x;
+      tile_pixel(p, a.H, a.W, b, y, x);
+      const bool live = p < a.M;
+      float hacc[kClasses];
+#pragma unroll
+      for (int k = 0; k < kClasses; ++k) hacc[k] = a.head_w ? head_s[kClasses * a.cout + k] : 0.f;
 #pragma unroll 1
       for (int c0 = 0; c0 < NT; c0 += 16) {
         uint32_t v[16];
@@ -276,31 +302,81 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
               "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (p < a.M) {
-          const int n = nt * NT + c0;
-          int co = n;
-          int64_t opix = p;
-          if (a.up) {
-            const int sub = n / a.cout;
-            co = n - sub * a.cout;
-            opix = (int64_t(b) * 2 * a.H + 2 * y + (sub >> 1)) * (2 * a.W) + 2 * x + (sub & 1);
-          }
-          uint32_t packed[8];
+        const int n = nt * NT + c0;
+        int co = n;
+        int64_t opix = (int64_t(b) * a.H + y) * a.W + x;
+        if (a.up) {
+          const int sub = n / a.cout;
+          co = n - sub * a.cout;
+          opix = (int64_t(b) * 2 * a.H + 2 * y + (sub >> 1)) * (2 * a.W) + 2 * x + (sub & 1);
+        }
+        uint32_t packed[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            float f0 = __uint_as_float(v[2 * e]) + bias_s[co + 2 * e];
-            float f1 = __uint_as_float(v[2 * e + 1]) + bias_s[co + 2 * e + 1];
-            if (a.relu) {
-              f0 = fmaxf(f0, 0.f);
-              f1 = fmaxf(f1, 0.f);
-            }
-            const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
-            packed[e] = *reinterpret_cast<const uint32_t*>(&h);
+        for (int e = 0; e < 8; ++e) {
+          float f0 = __uint_as_float(v[2 * e]) + bias_s[co + 2 * e];
+          float f1 = __uint_as_float(v[2 * e + 1]) + bias_s[co + 2 * e + 1];
+          if (a.relu) {
+            f0 = fmaxf(f0, 0.f);
+            f1 = fmaxf(f1, 0.f);
           }
+          const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+          packed[e] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        if (live && a.y) {
           uint4* dst = reinterpret_cast<uint4*>(a.y + opix * a.ys + co);
           dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
           dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
         }
+        if (a.head_w) {
+          // the head reads the stored (bf16) activation, channels in order
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&packed[e]));
+#pragma unroll
+            for (int k = 0; k < kClasses; ++k) {
+              hacc[k] = __fmaf_rn(f.x, head_s[k * a.cout + co + 2 * e], hacc[k]);
+              hacc[k] = __fmaf_rn(f.y, head_s[k * a.cout + co + 2 * e + 1], hacc[k]);
+            }
+          }
+        }
+        if (a.pool_y) {
+          // max over the 2x2 block held by lanes 4 m .. 4 m + 3
+          uint32_t m[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            uint32_t t1 = packed[e];
+            uint32_t o = __shfl_xor_sync(0xffffffffu, t1, 1);
+            __nv_bfloat162 mx = __hmax2(*reinterpret_cast<const __nv_bfloat162*>(&t1),
+                                        *reinterpret_cast<const __nv_bfloat162*>(&o));
+            t1 = *reinterpret_cast<const uint32_t*>(&mx);
+            o = __shfl_xor_sync(0xffffffffu, t1, 2);
+            mx = __hmax2(*reinterpret_cast<const __nv_bfloat162*>(&t1),
+                         *reinterpret_cast<const __nv_bfloat162*>(&o));
+            m[e] = *reinterpret_cast<const uint32_t*>(&mx);
+          }
+          if (live && (p & 3) == 0) {
+            uint4* dst = reinterpret_cast<uint4*>(a.pool_y + int64_t(p >> 2) * a.cout + co);
+            dst[0] = make_uint4(m[0], m[1], m[2], m[3]);
+            dst[1] = make_uint4(m[4], m[5], m[6], m[7]);
+          }
+        }
+      }
+      if (a.head_w && live) {
+        const float* sc = hacc;
+        int best = 0;
+        float top = sc[0];
+#pragma unroll
+        for (int k = 1; k < kClasses; ++k)
+          if (sc[k] > top) {
+            top = sc[k];
+            best = k;
+          }
+        const int64_t op = (int64_t(b) * a.H + y) * a.W + x;
+        if (a.logits) {
+#pragma unroll
+          for (int k = 0; k < kClasses; ++k) a.logits[op * kClasses + k] = sc[k];
+        }
+        if (a.labels) a.labels[op] = uint8_t(best);
       }
       // this accumulator may be overwritten by the tile after next
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -364,76 +440,8 @@ __global__ void k_prep(const uint8_t* __restrict__ chips, int64_t P, __nv_bfloat
   const uint8_t* s = chips + 3 * p;
   const __nv_bfloat162 rg = __floats2bfloat162_rn(s[0] * (1.f / 256.f), s[1] * (1.f / 256.f));
   const __nv_bfloat162 b0 = __floats2bfloat162_rn(s[2] * (1.f / 256.f), 0.f);
-  uint4 o;
-  o.x = *reinterpret_cast<const uint32_t*>(&rg);
-  o.y = *reinterpret_cast<const uint32_t*>(&b0);
-  o.z = 0;
-  o.w = 0;
-  reinterpret_cast<uint4*>(x)[p] = o;
-}
-
-// 2x2 max pooling; one thread per (output pixel, 8 channels).
-__global__ void k_pool(const __nv_bfloat16* __restrict__ x, int64_t xs, int H, int W, int C,
-                       int64_t n_out_px, __nv_bfloat16* __restrict__ y) {
-  const int groups = C >> 3;
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n_out_px * groups) return;
-  const int g = int(t % groups);
-  const int64_t q = t / groups;
-  const int Wo = W >> 1, Ho = H >> 1;
-  const int64_t b = q / (int64_t(Ho) * Wo);
-  const int rem = int(q - b * Ho * Wo), yo = rem / Wo, xo = rem - yo * Wo;
-  const int64_t p00 = (b * H + 2 * yo) * W + 2 * xo;
-  const int64_t offs[4] = {p00, p00 + 1, p00 + W, p00 + W + 1};
-  uint4 m;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint4 v = *reinterpret_cast<const uint4*>(x + offs[k] * xs + 8 * g);
-    if (k == 0) {
-      m = v;
-    } else {
-      __nv_bfloat162* mm = reinterpret_cast<__nv_bfloat162*>(&m);
-      const __nv_bfloat162* vv = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) mm[e] = __hmax2(mm[e], vv[e]);
-    }
-  }
-  *reinterpret_cast<uint4*>(y + q * C + 8 * g) = m;
-}
-
-// 1x1 head: 3 float32 scores per pixel, label = first largest.
-__global__ void k_head(const __nv_bfloat16* __restrict__ x, int F, int64_t P,
-                       const float* __restrict__ w, const float* __restrict__ bias,
-                       float* __restrict__ logits, uint8_t* __restrict__ labels) {
-  __shared__ float ws[kClasses * 64];
-  for (int i = threadIdx.x; i < kClasses * F; i += blockDim.x) ws[i] = w[i];
-  __syncthreads();
-  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  float acc[kClasses] = {bias[0], bias[1], bias[2]};
-  for (int c0 = 0; c0 < F; c0 += 8) {
-    const uint4 v = *reinterpret_cast<const uint4*>(x + p * F + c0);
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float2 f = __bfloat1622float2(h[e]);
-#pragma unroll
-      for (int k = 0; k < kClasses; ++k) {
-        acc[k] = __fmaf_rn(f.x, ws[k * F + c0 + 2 * e], acc[k]);
-        acc[k] = __fmaf_rn(f.y, ws[k * F + c0 + 2 * e + 1], acc[k]);
-      }
-    }
-  }
-  if (logits) {
-#pragma unroll
-    for (int k = 0; k < kClasses; ++k) logits[p * kClasses + k] = acc[k];
-  }
-  if (labels) {
-    int best = 0;
-    for (int k = 1; k < kClasses; ++k)
-      if (acc[k] > acc[best]) best = k;
-    labels[p] = uint8_t(best);
-  }
+  reinterpret_cast<uint4*>(x)[p] = make_uint4(*reinterpret_cast<const uint32_t*>(&rg),
+                                              *reinterpret_cast<const uint32_t*>(&b0), 0u, 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -452,6 +460,9 @@ struct Layer {
   float* bias = nullptr;
   Tensor in, out;
   bool relu = false;
+  int taps = 9;
+  __nv_bfloat16* pool = nullptr;  // fused 2x2 max pool output (encoder second convs)
+  bool head = false;              // fused 1x1 head (last decoder conv)
 };
 
 }  // namespace unet
@@ -463,10 +474,6 @@ struct sil_unet {
   std::vector<sil::unet::Layer> layers;
   std::vector<void*> allocs;
   __nv_bfloat16* x0 = nullptr;
-  struct Pool {
-    sil::unet::Tensor in, out;
-  };
-  std::vector<Pool> pools;
   float* head_w = nullptr;
   float* head_b = nullptr;
   unsigned int* err = nullptr;
@@ -537,7 +544,8 @@ cudaError_t launch_conv_nt(const ConvArgs& a, int mtiles, int ntiles, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t run_layer(const Layer& L, int n, unsigned int* err, cudaStream_t s) {
+cudaError_t run_layer(const Layer& L, int n, unsigned int* err, const float* head_w,
+                      const float* head_b, float* logits, uint8_t* labels, cudaStream_t s) {
   ConvArgs a;
   a.x = L.in.base;
   a.xs = L.in.stride;
@@ -553,6 +561,12 @@ cudaError_t run_layer(const Layer& L, int n, unsigned int* err, cudaStream_t s) 
   a.y = L.out.base;
   a.ys = L.out.stride;
   a.relu = L.relu;
+  a.taps = L.taps;
+  a.pool_y = L.pool;
+  a.head_w = L.head ? head_w : nullptr;
+  a.head_b = L.head ? head_b : nullptr;
+  a.logits = L.head ? logits : nullptr;
+  a.labels = L.head ? labels : nullptr;
   a.err = err;
   const int mtiles = (a.M + kBM - 1) / kBM, ntiles = L.N / L.NT;
   switch (L.NT) {
@@ -769,7 +783,8 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
     L.ci = int(up ? d[0] : d[1]);
     L.co = int(up ? d[1] : d[0]);
     L.cin_pad = L.ci < kInCh ? kInCh : L.ci;
-    L.K = up ? L.cin_pad : 9 * L.cin_pad;
+    L.taps = up ? 1 : 9;
+    L.K = L.taps == 1 ? L.cin_pad : 9 * L.cin_pad;
     L.KT = (L.K + kBK - 1) / kBK;
     L.N = up ? 4 * L.co : L.co;
     L.NT = L.N < 128 ? L.N : 128;
@@ -783,6 +798,7 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
       } else {
         L.in = t[l];
         L.out = skip_of(l);
+        L.pool = pool[l].base;
       }
     } else if (i == 2 * D) {
       L.in = pool[D - 1];
@@ -801,6 +817,7 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
       } else {
         L.in = d0[l];
         L.out = d1[l];
+        L.head = l == 0;
       }
     }
     // weights -> swizzled bf16 blocks [N / NT][KT][NT x 64]
@@ -830,7 +847,6 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
       st = SIL_ECUDA;
     net->layers.push_back(L);
   }
-  for (int l = 0; l < D; ++l) net->pools.push_back({skip_of(l), pool[l]});
   cudaSetDevice(prev);
   if (st != SIL_OK) {
     if (st == SIL_ECUDA) set_error("sil_unet_create: weight upload failed");
@@ -848,30 +864,14 @@ extern "C" sil_status sil_unet_forward(sil_unet* net, const uint8_t* chips, int3
     return SIL_EINVAL;
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int D = net->cfg.depth;
   const int64_t P = int64_t(n) * kChip * kChip;
   k_prep<<<unsigned((P + 255) / 256), 256, 0, s>>>(chips, P, net->x0);
   cudaError_t e = cudaGetLastError();
   const int nl = int(net->layers.size());
-  for (int i = 0; i < nl && e == cudaSuccess; ++i) {
-    const Layer& L = net->layers[i];
-    if (L.kind == SIL_UNET_HEAD) {
-      k_head<<<unsigned((P + 255) / 256), 256, 0, s>>>(L.in.base, net->cfg.base_width, P,
-                                                         net->head_w, net->head_b, logits, labels);
-      e = cudaGetLastError();
-      break;
-    }
-    e = run_layer(L, n, net->err, s);
-    // after the second conv of encoder level l: pool its output
-    if (e == cudaSuccess && i < 2 * D && i % 2 == 1) {
-      const auto& pl = net->pools[i / 2];
-      const int64_t out_px = int64_t(n) * pl.out.H * pl.out.W;
-      const int64_t threads = out_px * (pl.in.C / 8);
-      k_pool<<<unsigned((threads + 255) / 256), 256, 0, s>>>(pl.in.base, pl.in.stride, pl.in.H, pl.in.W,
-                                                             pl.in.C, out_px, pl.out.base);
-      e = cudaGetLastError();
-    }
-  }
+  // the head is fused into the last decoder convolution, the pooling into
+  // the encoders' second convolutions
+  for (int i = 0; i < nl - 1 && e == cudaSuccess; ++i)
+    e = run_layer(net->layers[i], n, net->err, net->head_w, net->head_b, logits, labels, s);
   if (e != cudaSuccess) {
     set_error("sil_unet_forward: launch failed: %s", cudaGetErrorString(e));
     return SIL_ECUDA;
