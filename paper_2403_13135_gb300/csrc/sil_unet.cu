@@ -21,6 +21,7 @@
 // the bias, applies ReLU, rounds to bfloat16 and stores channels-last.
 // Every wait is bounded; a wait that runs out counts an error and the CTA
 // still frees its tensor memory.
+#include <cuda.h>  // CUtensorMap (the encoder is fetched at run time, no -lcuda)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -67,19 +68,20 @@ struct ConvArgs {
   const float* head_b;     // ... and its bias; needs NT == cout
   float* logits;           // head scores [n][H][W][3] (nullable)
   uint8_t* labels;         // head argmax [n][H][W] (nullable)
+  int tma;                 // 1: A tiles by tensor-map loads (Ci multiple of 64)
   unsigned int* err;       // count of bounded waits that ran out
 };
 
-// Tiles walk the pixels in 2x2 blocks: tile index p (0 .. n H W - 1) is
-// pixel (2 Y + s / 2, 2 X + s % 2) of block q = p / 4 = (b, Y, X) row-major,
-// s = p % 4.  A 2x2 pooling window is then 4 adjacent rows of a tile (4
-// adjacent lanes of an epilogue warp), and the pooled pixel's index is q.
-__device__ __forceinline__ void tile_pixel(int p, int H, int W, int& b, int& y, int& x) {
-  const int q = p >> 2, s = p & 3, Wb = W >> 1, HWb = (H >> 1) * Wb;
-  b = q / HWb;
-  const int rem = q - b * HWb, Y = rem / Wb, X = rem - Y * Wb;
-  y = 2 * Y + (s >> 1);
-  x = 2 * X + (s & 1);
+// A tile is 8 image rows x 16 pixels of one image: tile row r is pixel
+// (y0 + r / 16, x0 + r % 16).  A 2x2 pooling window is then lanes l, l ^ 1,
+// l ^ 16, l ^ 17 of one epilogue warp.
+constexpr int kTileW = 16, kTileH = 8;
+__device__ __forceinline__ void tile_origin(int mt, int H, int W, int& b, int& y0, int& x0) {
+  const int tx = W / kTileW, per_img = (H / kTileH) * tx;
+  b = mt / per_img;
+  const int rem = mt - b * per_img, ty = rem / tx;
+  y0 = ty * kTileH;
+  x0 = (rem - ty * tx) * kTileW;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -150,7 +152,8 @@ struct ConvCfg {
 // t / ntiles, N tile t % ntiles).  Warps 0-3 produce A/B stages, warps 4-7
 // drain the accumulators, warp 8 issues the MMAs.
 template <int NT>
-__global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int ntiles, int ntotal) {
+__global__ void __launch_bounds__(kConvThreads, 2)
+    k_conv(const ConvArgs a, const __grid_constant__ CUtensorMap tmap, int ntiles, int ntotal) {
   using C = ConvCfg<NT>;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
       head_s[i] = i < kClasses * a.cout ? a.head_w[i] : a.head_b[i - kClasses * a.cout];
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), kProducers + 1);
+      mbar_init(smem_u32(&full_bar[s]), a.tma ? 1 : kProducers + 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -190,8 +193,55 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  if (warp < 4) {
-    // ---- producers: rows 32 warp + 4 i + lane / 8, 16-byte chunk lane % 8
+  if (warp < 4 && a.tma) {
+    // ---- producer, tensor-map path (one thread): per stage one box of
+    // 8 x 16 pixels x 64 channels at the tap's offset (zero outside the
+    // image, written by the TMA unit in the 128-byte swizzled layout) and the
+    // weight block
+    if (tid == 0) {
+      const int cmask = (1 << a.cin_log2) - 1;
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntotal && ok; t += gridDim.x) {
+        const int mt = t / ntiles, nt = t - mt * ntiles;
+        int b, y0, x0;
+        tile_origin(mt, a.H, a.W, b, y0, x0);
+        for (int kt = 0; kt < a.KT; ++kt, ++it) {
+          const int s = it % S;
+          if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), uint32_t((it / S - 1) & 1), failed)) {
+            give_up(failed, a.err);
+            ok = false;
+            break;
+          }
+          const int k0 = kt * kBK;
+          const int tap = a.taps == 1 ? 4 : (k0 >> a.cin_log2);
+          const int c0 = a.taps == 1 ? k0 : (k0 & cmask);
+          const uint32_t a_s = smem_u32(smem + s * C::kStage), fb = smem_u32(&full_bar[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                       "r"(uint32_t(C::kA + C::kB))
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+                  a_s),
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(c0), "r"(x0 + tap % 3 - 1), "r"(y0 + tap / 3 - 1),
+              "r"(b), "r"(fb)
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  a_s + uint32_t(C::kA)),
+              "l"(a.wblk + (size_t(nt) * a.KT + kt) * C::kB), "r"(uint32_t(C::kB)), "r"(fb)
+              : "memory");
+        }
+      }
+      for (int i = it - S; ok && i < it; ++i)
+        if (i >= 0 && !mbar_wait(smem_u32(&empty_bar[i % S]), uint32_t((i / S) & 1), failed)) {
+          give_up(failed, a.err);
+          ok = false;
+        }
+    }
+  } else if (warp < 4) {
+    // ---- producers, gather path: rows 32 warp + 4 i + lane / 8, 16-byte
+    // chunk lane % 8
     const int j = lane & 7;
     uint32_t soff[8];
 #pragma unroll
@@ -208,15 +258,16 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
       // (bit 0 above, 1 below, 2 left, 3 right, 4 the pixel itself)
       int64_t pbase[8];
       uint32_t pfl[8];
+      int b, y0, x0;
+      tile_origin(mt, a.H, a.W, b, y0, x0);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int p = mt * kBM + 32 * warp + 4 * i + (lane >> 3);
-        int b, y, x;
-        tile_pixel(p, a.H, a.W, b, y, x);
+        const int r = 32 * warp + 4 * i + (lane >> 3);
+        const int y = y0 + (r >> 4), x = x0 + (r & 15);
         pbase[i] = ((int64_t(b) * a.H + y) * a.W + x) * a.xs;
-        pfl[i] = p < a.M ? (16u | (y > 0 ? 1u : 0u) | (y < a.H - 1 ? 2u : 0u) |
-                            (x > 0 ? 4u : 0u) | (x < a.W - 1 ? 8u : 0u))
-                         : 0u;
+        pfl[i] = mt * kBM + r < a.M ? (16u | (y > 0 ? 1u : 0u) | (y < a.H - 1 ? 2u : 0u) |
+                                       (x > 0 ? 4u : 0u) | (x < a.W - 1 ? 8u : 0u))
+                                    : 0u;
       }
       for (int kt = 0; kt < a.KT; ++kt, ++it) {
         const int s = it % S;
@@ -285,8 +336,9 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int p = mt * kBM + r;
-      int b, y, x;
-      tile_pixel(p, a.H, a.W, b, y, x);
+      int b, y0, x0;
+      tile_origin(mt, a.H, a.W, b, y0, x0);
+      const int y = y0 + (r >> 4), x = x0 + (r & 15);
       const bool live = p < a.M;
       float hacc[kClasses];
 #pragma unroll
@@ -340,7 +392,7 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
           }
         }
         if (a.pool_y) {
-          // max over the 2x2 block held by lanes 4 m .. 4 m + 3
+          // max over the 2x2 block held by lanes l, l ^ 1, l ^ 16, l ^ 17
           uint32_t m[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -349,13 +401,14 @@ __global__ void __launch_bounds__(kConvThreads, 2) k_conv(const ConvArgs a, int 
             __nv_bfloat162 mx = __hmax2(*reinterpret_cast<const __nv_bfloat162*>(&t1),
                                         *reinterpret_cast<const __nv_bfloat162*>(&o));
             t1 = *reinterpret_cast<const uint32_t*>(&mx);
-            o = __shfl_xor_sync(0xffffffffu, t1, 2);
+            o = __shfl_xor_sync(0xffffffffu, t1, 16);
             mx = __hmax2(*reinterpret_cast<const __nv_bfloat162*>(&t1),
                          *reinterpret_cast<const __nv_bfloat162*>(&o));
             m[e] = *reinterpret_cast<const uint32_t*>(&mx);
           }
-          if (live && (p & 3) == 0) {
-            uint4* dst = reinterpret_cast<uint4*>(a.pool_y + int64_t(p >> 2) * a.cout + co);
+          if (live && (lane & 17) == 0) {
+            const int64_t q = (int64_t(b) * (a.H >> 1) + (y >> 1)) * (a.W >> 1) + (x >> 1);
+            uint4* dst = reinterpret_cast<uint4*>(a.pool_y + q * a.cout + co);
             dst[0] = make_uint4(m[0], m[1], m[2], m[3]);
             dst[1] = make_uint4(m[4], m[5], m[6], m[7]);
           }
@@ -463,6 +516,8 @@ struct Layer {
   int taps = 9;
   __nv_bfloat16* pool = nullptr;  // fused 2x2 max pool output (encoder second convs)
   bool head = false;              // fused 1x1 head (last decoder conv)
+  bool tma = false;               // A tiles through a tensor map (Ci % 64 == 0)
+  CUtensorMap tmap{};             // 4-D map of the input: {Ci, W, H, max_batch}
 };
 
 }  // namespace unet
@@ -509,8 +564,48 @@ size_t sw128_off(int rr, int k) {
          size_t(k & 7) * 2;
 }
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a layer's input {Ci, W, H, batch} (channels-last, pixel
+// stride xs elements), box 64 channels x 16 x 8 pixels, 128-byte swizzle,
+// zero fill outside.
+bool encode_input_map(Layer& L, int batch) {
+  const EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {cuuint64_t(L.cin_pad), cuuint64_t(L.in.W), cuuint64_t(L.in.H),
+                              cuuint64_t(batch)};
+  const cuuint64_t es = 2;
+  const cuuint64_t strides[3] = {cuuint64_t(L.in.stride) * es, cuuint64_t(L.in.W) * L.in.stride * es,
+                                 cuuint64_t(L.in.H) * L.in.W * L.in.stride * es};
+  const cuuint32_t box[4] = {cuuint32_t(kBK), cuuint32_t(kTileW), cuuint32_t(kTileH), 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(&L.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, L.in.base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int NT>
-cudaError_t launch_conv_nt(const ConvArgs& a, int mtiles, int ntiles, cudaStream_t s) {
+cudaError_t launch_conv_nt(const ConvArgs& a, const CUtensorMap& tmap, int mtiles, int ntiles,
+                           cudaStream_t s) {
   static int ctas_per_sm = 0;  // per process; set before the first launch
   static int sms = 0;
   if (!ctas_per_sm) {
@@ -540,7 +635,7 @@ cudaError_t launch_conv_nt(const ConvArgs& a, int mtiles, int ntiles, cudaStream
   const int ntotal = mtiles * ntiles;
   const int cap = sms * ctas_per_sm;
   const int grid = ntotal < cap ? ntotal : cap;
-  k_conv<NT><<<grid, kConvThreads, ConvCfg<NT>::kSmem, s>>>(a, ntiles, ntotal);
+  k_conv<NT><<<grid, kConvThreads, ConvCfg<NT>::kSmem, s>>>(a, tmap, ntiles, ntotal);
   return cudaGetLastError();
 }
 
@@ -567,13 +662,14 @@ cudaError_t run_layer(const Layer& L, int n, unsigned int* err, const float* hea
   a.head_b = L.head ? head_b : nullptr;
   a.logits = L.head ? logits : nullptr;
   a.labels = L.head ? labels : nullptr;
+  a.tma = L.tma ? 1 : 0;
   a.err = err;
   const int mtiles = (a.M + kBM - 1) / kBM, ntiles = L.N / L.NT;
   switch (L.NT) {
-    case 16: return launch_conv_nt<16>(a, mtiles, ntiles, s);
-    case 32: return launch_conv_nt<32>(a, mtiles, ntiles, s);
-    case 64: return launch_conv_nt<64>(a, mtiles, ntiles, s);
-    default: return launch_conv_nt<128>(a, mtiles, ntiles, s);
+    case 16: return launch_conv_nt<16>(a, L.tmap, mtiles, ntiles, s);
+    case 32: return launch_conv_nt<32>(a, L.tmap, mtiles, ntiles, s);
+    case 64: return launch_conv_nt<64>(a, L.tmap, mtiles, ntiles, s);
+    default: return launch_conv_nt<128>(a, L.tmap, mtiles, ntiles, s);
   }
 }
 
@@ -787,6 +883,7 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
     L.K = L.taps == 1 ? L.cin_pad : 9 * L.cin_pad;
     L.KT = (L.K + kBK - 1) / kBK;
     L.N = up ? 4 * L.co : L.co;
+    L.tma = L.cin_pad % kBK == 0;
     L.NT = L.N < 128 ? L.N : 128;
     L.relu = !up;
     // inputs and outputs
@@ -820,6 +917,8 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
         L.head = l == 0;
       }
     }
+    // inputs whose channel count is a multiple of 64 are read by tensor map
+    if (L.tma && !encode_input_map(L, B)) L.tma = false;
     // weights -> swizzled bf16 blocks [N / NT][KT][NT x 64]
     const size_t blk = size_t(L.NT) * kBK * 2;
     std::vector<uint8_t> h(size_t(L.N / L.NT) * L.KT * blk, 0);
