@@ -68,7 +68,9 @@ struct ConvArgs {
   const float* head_b;     // ... and its bias; needs NT == cout
   float* logits;           // head scores [n][H][W][3] (nullable)
   uint8_t* labels;         // head argmax [n][H][W] (nullable)
-  int tma;                 // 1: A tiles by tensor-map loads (Ci multiple of 64)
+  int tma;                 // A tiles by tensor-map loads: 0 no (per-row gather),
+                           // 1 one 64-channel box per stage (Ci multiple of 64),
+                           // 2 two 32-channel boxes (two taps) per stage (Ci = 32)
   unsigned int* err;       // count of bounded waits that ran out
 };
 
@@ -130,6 +132,12 @@ __device__ __forceinline__ void give_up(volatile int* failed, unsigned int* err)
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   return uint64_t((addr & 0x3FFFFu) >> 4) | (uint64_t(16 >> 4) << 16) |
          (uint64_t(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// 64-byte swizzle, K-major: rows of 64 bytes, 8-row atoms of 512 bytes.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  return uint64_t((addr & 0x3FFFFu) >> 4) | (uint64_t(16 >> 4) << 16) |
+         (uint64_t(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
 template <int NT>
@@ -214,18 +222,31 @@ __global__ void __launch_bounds__(kConvThreads, 2)
             break;
           }
           const int k0 = kt * kBK;
-          const int tap = a.taps == 1 ? 4 : (k0 >> a.cin_log2);
-          const int c0 = a.taps == 1 ? k0 : (k0 & cmask);
           const uint32_t a_s = smem_u32(smem + s * C::kStage), fb = smem_u32(&full_bar[s]);
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
                        "r"(uint32_t(C::kA + C::kB))
                        : "memory");
-          asm volatile(
-              "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
-                  a_s),
-              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(c0), "r"(x0 + tap % 3 - 1), "r"(y0 + tap / 3 - 1),
-              "r"(b), "r"(fb)
-              : "memory");
+          // mode 1: one box, tap k0 / Ci, channels k0 % Ci .. + 63; mode 2:
+          // taps 2 kt and 2 kt + 1, all 32 channels each (a tap past the
+          // ninth is a box far outside the image: zeros)
+          const int nbox = a.tma == 2 ? 2 : 1;
+          for (int bx = 0; bx < nbox; ++bx) {
+            int tap, c0;
+            if (a.tma == 2) {
+              tap = 2 * kt + bx;
+              c0 = 0;
+            } else {
+              tap = a.taps == 1 ? 4 : (k0 >> a.cin_log2);
+              c0 = a.taps == 1 ? k0 : (k0 & cmask);
+            }
+            const int yy = tap < 9 ? y0 + tap / 3 - 1 : -4 * kTileH;
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+                    a_s + uint32_t(bx * (C::kA / 2))),
+                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(c0), "r"(x0 + tap % 3 - 1), "r"(yy),
+                "r"(b), "r"(fb)
+                : "memory");
+          }
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                   a_s + uint32_t(C::kA)),
@@ -460,7 +481,11 @@ __global__ void __launch_bounds__(kConvThreads, 2)
         const uint32_t a0 = smem_u32(smem + s * C::kStage), b0 = a0 + uint32_t(C::kA);
 #pragma unroll
         for (int kk = 0; kk < kBK / 16; ++kk) {
-          const uint64_t ad = sw128_desc(a0 + 32 * kk), bd = sw128_desc(b0 + 32 * kk);
+          // A: 128-byte rows (one box or the per-row gather), or with two
+          // 32-channel boxes, box kk / 2 at 32 bytes per K slice
+          const uint64_t ad = a.tma == 2 ? sw64_desc(a0 + uint32_t((kk >> 1) * (C::kA / 2) + 32 * (kk & 1)))
+                                         : sw128_desc(a0 + 32 * kk);
+          const uint64_t bd = sw128_desc(b0 + 32 * kk);
           const uint32_t acc = (kt | kk) ? 1u : 0u;
           asm volatile(
               "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
@@ -516,7 +541,7 @@ struct Layer {
   int taps = 9;
   __nv_bfloat16* pool = nullptr;  // fused 2x2 max pool output (encoder second convs)
   bool head = false;              // fused 1x1 head (last decoder conv)
-  bool tma = false;               // A tiles through a tensor map (Ci % 64 == 0)
+  int tma = 0;                    // A tiles through a tensor map (see ConvArgs::tma)
   CUtensorMap tmap{};             // 4-D map of the input: {Ci, W, H, max_batch}
 };
 
@@ -586,8 +611,8 @@ EncodeTiledFn tensor_map_encoder() {
 }
 
 // Tensor map of a layer's input {Ci, W, H, batch} (channels-last, pixel
-// stride xs elements), box 64 channels x 16 x 8 pixels, 128-byte swizzle,
-// zero fill outside.
+// stride xs elements), box 64 channels x 16 x 8 pixels with 128-byte swizzle
+// (mode 1) or 32 channels with 64-byte swizzle (mode 2); zero fill outside.
 bool encode_input_map(Layer& L, int batch) {
   const EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return false;
@@ -596,10 +621,12 @@ bool encode_input_map(Layer& L, int batch) {
   const cuuint64_t es = 2;
   const cuuint64_t strides[3] = {cuuint64_t(L.in.stride) * es, cuuint64_t(L.in.W) * L.in.stride * es,
                                  cuuint64_t(L.in.H) * L.in.W * L.in.stride * es};
-  const cuuint32_t box[4] = {cuuint32_t(kBK), cuuint32_t(kTileW), cuuint32_t(kTileH), 1};
+  const cuuint32_t box[4] = {cuuint32_t(L.tma == 2 ? kBK / 2 : kBK), cuuint32_t(kTileW),
+                             cuuint32_t(kTileH), 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return enc(&L.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, L.in.base, dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE,
+             L.tma == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -662,7 +689,7 @@ cudaError_t run_layer(const Layer& L, int n, unsigned int* err, const float* hea
   a.head_b = L.head ? head_b : nullptr;
   a.logits = L.head ? logits : nullptr;
   a.labels = L.head ? labels : nullptr;
-  a.tma = L.tma ? 1 : 0;
+  a.tma = L.tma;
   a.err = err;
   const int mtiles = (a.M + kBM - 1) / kBM, ntiles = L.N / L.NT;
   switch (L.NT) {
@@ -883,7 +910,7 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
     L.K = L.taps == 1 ? L.cin_pad : 9 * L.cin_pad;
     L.KT = (L.K + kBK - 1) / kBK;
     L.N = up ? 4 * L.co : L.co;
-    L.tma = L.cin_pad % kBK == 0;
+    L.tma = (L.cin_pad % kBK == 0) ? 1 : (L.cin_pad == kBK / 2 && !up) ? 2 : 0;
     L.NT = L.N < 128 ? L.N : 128;
     L.relu = !up;
     // inputs and outputs
@@ -918,7 +945,7 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
       }
     }
     // inputs whose channel count is a multiple of 64 are read by tensor map
-    if (L.tma && !encode_input_map(L, B)) L.tma = false;
+    if (L.tma && !encode_input_map(L, B)) L.tma = 0;
     // weights -> swizzled bf16 blocks [N / NT][KT][NT x 64]
     const size_t blk = size_t(L.NT) * kBK * 2;
     std::vector<uint8_t> h(size_t(L.N / L.NT) * L.KT * blk, 0);
