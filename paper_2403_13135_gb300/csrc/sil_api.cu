@@ -340,8 +340,14 @@ sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
   return SIL_OK;
 }
 
-// Host-buffer variant: per-thread cached device staging buffers.
+// Host-buffer variant: per-thread cached device staging buffers, two copy
+// streams and per-stripe events.  The image is cut into stripes of whole
+// chip rows; stripe i is copied in on one stream while stripe i-1 is
+// labelled on the caller's stream and the labels of stripe i-2 are copied
+// out on the other, so the call costs about one pass over the host link.
+constexpr int kMaxStripes = 64;
 struct HostStage {
+  int device = -1;
   void* img = nullptr;
   size_t img_bytes = 0;
   uint8_t* lab = nullptr;
@@ -349,12 +355,31 @@ struct HostStage {
   uint64_t* cnt = nullptr;
   uint32_t* cc = nullptr;
   size_t cc_bytes = 0;
-  ~HostStage() {
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, ev_in[kMaxStripes] = {}, ev_done[kMaxStripes] = {};
+  void release() {
     cudaFree(img);
     cudaFree(lab);
     cudaFree(cnt);
     cudaFree(cc);
+    if (in) cudaStreamDestroy(in);
+    if (out) cudaStreamDestroy(out);
+    if (start) cudaEventDestroy(start);
+    for (int i = 0; i < kMaxStripes; ++i) {
+      if (ev_in[i]) cudaEventDestroy(ev_in[i]);
+      if (ev_done[i]) cudaEventDestroy(ev_done[i]);
+      ev_in[i] = ev_done[i] = nullptr;
+    }
+    device = -1;
+    img = nullptr;
+    lab = nullptr;
+    cnt = nullptr;
+    cc = nullptr;
+    img_bytes = lab_bytes = cc_bytes = 0;
+    in = out = nullptr;
+    start = nullptr;
   }
+  ~HostStage() { release(); }
 };
 static thread_local HostStage g_stage;
 
@@ -372,6 +397,30 @@ static sil_status ensure(void** p, size_t* have, size_t need) {
   return SIL_OK;
 }
 
+// Streams and events of the pipeline, created once per thread and device.
+static sil_status ensure_pipe(HostStage& g) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_error("sil_label_host: no current device");
+    return SIL_ECUDA;
+  }
+  if (g.device != dev) g.release();  // buffers of another device
+  g.device = dev;
+  if (g.in) return SIL_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&g.in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.start, cudaEventDisableTiming);
+  for (int i = 0; i < kMaxStripes && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&g.ev_in[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.ev_done[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    g.release();
+    return cuda_fail(e, "sil_label_host: stream/event setup");
+  }
+  return SIL_OK;
+}
+
 sil_status sil_label_host(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
                           sil_dtype dt, const sil_params* p, uint8_t* labels,
                           int64_t label_pitch, uint64_t* counts,
@@ -384,10 +433,13 @@ sil_status sil_label_host(const void* img, int64_t H, int64_t W, int64_t pitch_b
   if (st != SIL_OK) return st;
   const int chip = p ? p->chip : 256;
   const int64_t bpp = dt == SIL_U8 ? 3 : 6;
-  const int64_t dpitch = ((W * bpp + 127) / 128) * 128;
+  const int64_t row_bytes = W * bpp;
   const int64_t gx = (W + chip - 1) / chip, gy = (H + chip - 1) / chip;
   HostStage& g = g_stage;
-  if ((st = ensure(&g.img, &g.img_bytes, size_t(dpitch * H))) != SIL_OK) return st;
+  if ((st = ensure_pipe(g)) != SIL_OK) return st;
+  // the device copy keeps the host pitch, so each stripe is one contiguous
+  // range when the host rows are dense
+  if ((st = ensure(&g.img, &g.img_bytes, size_t(pitch_bytes * H))) != SIL_OK) return st;
   if (labels && (st = ensure(reinterpret_cast<void**>(&g.lab), &g.lab_bytes, size_t(W * H))) != SIL_OK)
     return st;
   size_t cnt_bytes = g.cnt ? 32 : 0;
@@ -396,24 +448,66 @@ sil_status sil_label_host(const void* img, int64_t H, int64_t W, int64_t pitch_b
       (st = ensure(reinterpret_cast<void**>(&g.cc), &g.cc_bytes, size_t(gx * gy * 16))) != SIL_OK)
     return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpy2DAsync(g.img, dpitch, img, pitch_bytes, W * bpp, H,
-                                    cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: copy in");
-  st = sil_label(g.img, H, W, dpitch, dt, p, labels ? g.lab : nullptr, W, g.cnt,
-                 chip_counts ? g.cc : nullptr, stream);
-  if (st != SIL_OK) return st;
-  if (labels) {
-    e = cudaMemcpy2DAsync(labels, label_pitch, g.lab, W, W, H, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: copy labels out");
+  uint8_t* dimg = static_cast<uint8_t*>(g.img);
+  const uint8_t* himg = static_cast<const uint8_t*>(img);
+  // about 12 stripes of whole chip rows
+  int64_t ks = gy / 12;
+  if (ks < 1) ks = 1;
+  if ((gy + ks - 1) / ks > kMaxStripes) ks = (gy + kMaxStripes - 1) / kMaxStripes;
+  const int nstripes = int((gy + ks - 1) / ks);
+  Req r;
+  r.W = W;
+  r.pitch = pitch_bytes;
+  r.lpitch = W;
+  r.counts = reinterpret_cast<unsigned long long*>(g.cnt);
+  r.gx = int32_t(gx);
+  r.chip_begin = 0;
+  const int64_t cap = int64_t(device_sm_count()) * 16;
+  cudaError_t e = cudaEventRecord(g.start, s);  // the copies follow earlier work on s
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g.in, g.start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g.out, g.start, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.cnt, 0, 32, s);
+  for (int i = 0; i < nstripes && e == cudaSuccess; ++i) {
+    const int64_t r0 = int64_t(i) * ks * chip;
+    const int64_t r1 = r0 + ks * chip < H ? r0 + ks * chip : H;
+    const int64_t rows = r1 - r0;
+    // copy in (the last row only up to its last pixel)
+    if (pitch_bytes == row_bytes)
+      e = cudaMemcpyAsync(dimg + r0 * pitch_bytes, himg + r0 * pitch_bytes, size_t(rows * row_bytes),
+                          cudaMemcpyHostToDevice, g.in);
+    else
+      e = cudaMemcpy2DAsync(dimg + r0 * pitch_bytes, pitch_bytes, himg + r0 * pitch_bytes, pitch_bytes,
+                            row_bytes, rows, cudaMemcpyHostToDevice, g.in);
+    if (e == cudaSuccess) e = cudaEventRecord(g.ev_in[i], g.in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g.ev_in[i], 0);
+    if (e != cudaSuccess) break;
+    // label the stripe; counts accumulate, chip counts land at its chip rows
+    r.img = dimg + r0 * pitch_bytes;
+    r.H = rows;
+    r.labels = labels ? g.lab + r0 * W : nullptr;
+    r.chip_counts = chip_counts ? g.cc + (r0 / chip) * gx * 4 : nullptr;
+    r.gy = int32_t((rows + chip - 1) / chip);
+    const int64_t nchips = int64_t(r.gx) * r.gy;
+    e = launch_label(r, dt, dp, chip, int(nchips < cap ? nchips : cap), s);
+    if (e == cudaSuccess) e = cudaEventRecord(g.ev_done[i], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g.out, g.ev_done[i], 0);
+    if (e == cudaSuccess && labels) {
+      if (label_pitch == W)
+        e = cudaMemcpyAsync(labels + r0 * W, g.lab + r0 * W, size_t(rows * W), cudaMemcpyDeviceToHost,
+                            g.out);
+      else
+        e = cudaMemcpy2DAsync(labels + r0 * label_pitch, label_pitch, g.lab + r0 * W, W, W, rows,
+                              cudaMemcpyDeviceToHost, g.out);
+    }
   }
-  e = cudaMemcpyAsync(counts, g.cnt, 32, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: copy counts out");
-  if (chip_counts) {
-    e = cudaMemcpyAsync(chip_counts, g.cc, size_t(gx * gy * 16), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: copy chip counts out");
-  }
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "sil_label_host: synchronize");
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts, g.cnt, 32, cudaMemcpyDeviceToHost, g.out);
+  if (e == cudaSuccess && chip_counts)
+    e = cudaMemcpyAsync(chip_counts, g.cc, size_t(gx * gy * 16), cudaMemcpyDeviceToHost, g.out);
+  // the out stream ends after every stripe's kernel and copy
+  const cudaError_t es = cudaStreamSynchronize(g.out);
+  const cudaError_t es2 = cudaStreamSynchronize(g.in);
+  if (e == cudaSuccess) e = es != cudaSuccess ? es : es2;
+  if (e != cudaSuccess) return cuda_fail(e, "sil_label_host");
   return SIL_OK;
 }
 

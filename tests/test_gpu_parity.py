@@ -183,6 +183,33 @@ def test_host_buffer_entry_point(sil):
     np.testing.assert_array_equal(cc, occ)
 
 
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_host_entry_point_striped(sil, dtype):
+    """The host entry point pipelines stripes of whole chip rows (copy in,
+    label, copy out on three streams): a tall image of many stripes, host
+    rows with padding, a label pitch wider than W, a chip of 100."""
+    img, _ = synth.scene(2900, 300, 5, n_floes=8, dtype=dtype)
+    bpp = img.dtype.itemsize * 3
+    host = np.zeros((2900, 300 * bpp + 16), np.uint8)
+    host[:, :300 * bpp] = img.view(np.uint8).reshape(2900, 300 * bpp)
+    view = host[:, :300 * bpp].view(img.dtype).reshape(2900, 300, 3)
+    assert view.strides[0] == 300 * bpp + 16
+    p = dict(oracle.params_default(), chip=100)
+    pp = sil.params(chip=100)
+    lab = np.full((2900, 320), 7, np.uint8)
+    cnt = np.zeros(4, np.uint64)
+    cc = np.zeros((29, 3, 4), np.uint32)
+    import ctypes
+    dt = sil.SIL_U8 if dtype == np.uint8 else sil.SIL_U16
+    sil.check(sil.sil_label_host(view.ctypes.data, 2900, 300, view.strides[0], dt, ctypes.byref(pp),
+                                 lab.ctypes.data, 320, cnt.ctypes.data, cc.ctypes.data, None))
+    olab, ocnt, occ, _ = oracle.label(np.ascontiguousarray(view), p)
+    assert int((lab[:, :300] != olab).sum()) == 0
+    assert np.all(lab[:, 300:] == 7)          # bytes past W untouched
+    np.testing.assert_array_equal(cnt, ocnt)
+    np.testing.assert_array_equal(cc, occ)
+
+
 def test_full_scene_sampled_chips(sil):
     """The 10980 x 10980 scene in the benchmark's launch configuration:
     per-chip counts of sampled chips and their labels against the oracle run
