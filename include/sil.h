@@ -130,11 +130,14 @@ sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
                      uint32_t* chip_counts, sil_stream stream);
 
 /* Same as sil_label but the image, labels and counts are HOST buffers; the
- * library stages them through its own device buffers (pitched copy in,
- * labels and counts back) on `stream` and returns when the results are in
- * host memory.  Pinned host memory gives the fastest copies.  labels and
- * chip_counts may be NULL.  Device buffers are cached per host thread and
- * reused across calls. */
+ * library stages them through its own device buffers and returns when the
+ * results are in host memory.  The image is cut into stripes of whole chip
+ * rows: the copy in of a stripe, the labelling of the previous one (on
+ * `stream`) and the copy back of the one before run concurrently (two
+ * internal streams ordered after earlier work on `stream`).  Pinned host
+ * memory gives the fastest copies.  labels and chip_counts may be NULL.
+ * Device buffers, streams and events are cached per host thread and device
+ * and reused across calls. */
 sil_status sil_label_host(const void* img, int64_t H, int64_t W,
                           int64_t pitch_bytes, sil_dtype dt, const sil_params* p,
                           uint8_t* labels, int64_t label_pitch,

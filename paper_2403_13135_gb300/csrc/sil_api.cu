@@ -346,6 +346,9 @@ sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
 // labelled on the caller's stream and the labels of stripe i-2 are copied
 // out on the other, so the call costs about one pass over the host link.
 constexpr int kMaxStripes = 64;
+#ifndef SIL_HOST_STRIPES
+#define SIL_HOST_STRIPES 12
+#endif
 struct HostStage {
   int device = -1;
   void* img = nullptr;
@@ -450,8 +453,8 @@ sil_status sil_label_host(const void* img, int64_t H, int64_t W, int64_t pitch_b
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   uint8_t* dimg = static_cast<uint8_t*>(g.img);
   const uint8_t* himg = static_cast<const uint8_t*>(img);
-  // about 12 stripes of whole chip rows
-  int64_t ks = gy / 12;
+  // about SIL_HOST_STRIPES stripes of whole chip rows
+  int64_t ks = gy / SIL_HOST_STRIPES;
   if (ks < 1) ks = 1;
   if ((gy + ks - 1) / ks > kMaxStripes) ks = (gy + kMaxStripes - 1) / kMaxStripes;
   const int nstripes = int((gy + ks - 1) / ks);
