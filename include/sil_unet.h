@@ -97,6 +97,14 @@ sil_status sil_unet_forward(sil_unet* net, const uint8_t* chips, int32_t n, uint
  * out since the network was created (0 in normal operation). */
 sil_status sil_unet_error_count(sil_unet* net, uint32_t* count);
 
+/* Test hook for the bounded waits: while set, every CTA of layer `layer`'s
+ * kernel leaves out the input load of its first stage, so the wait for that
+ * stage runs out (about 1.3 s), the kernel counts an error, frees its tensor
+ * memory and returns (that layer's output is then undefined).  layer = -1
+ * clears the hook.  Only layers whose input arrives by tensor map (input
+ * channels 32 or a multiple of 64) take it; others: SIL_EINVAL. */
+sil_status sil_unet_set_fault(sil_unet* net, int32_t layer);
+
 /* Output activation of layer i (sil_unet_layer_shape order) of the last
  * forward pass: dims = {n, H, W, C} (n of that pass).  i = -1: the prepared
  * input, 8 channels (R, G, B scaled by 1/256, then 5 zeros).  The head (the

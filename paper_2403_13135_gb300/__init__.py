@@ -113,6 +113,7 @@ _SIGS = {
     "sil_unet_destroy": ([_P], None),
     "sil_unet_forward": ([_P, _P, _I32, _P, _P, _P], _I32),
     "sil_unet_error_count": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I32),
+    "sil_unet_set_fault": ([_P, _I32], _I32),
     "sil_unet_tensor_shape": ([_P, _I32, ctypes.POINTER(_I64)], _I32),
     "sil_unet_copy_tensor": ([_P, _I32, _P, _P], _I32),
 }
@@ -454,6 +455,10 @@ class UNet:
                                     labels.data_ptr() if labels is not None else None,
                                     logits.data_ptr() if logits is not None else None,
                                     _stream_handle(stream)))
+
+    def set_fault(self, layer: int) -> None:
+        """Test hook: make layer `layer`'s bounded wait run out (-1 clears)."""
+        check(_lib.sil_unet_set_fault(self.handle, int(layer)))
 
     def error_count(self) -> int:
         v = ctypes.c_uint32()

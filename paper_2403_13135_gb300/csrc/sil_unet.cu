@@ -71,6 +71,7 @@ struct ConvArgs {
   int tma;                 // A tiles by tensor-map loads: 0 no (per-row gather),
                            // 1 one 64-channel box per stage (Ci multiple of 64),
                            // 2 two 32-channel boxes (two taps) per stage (Ci = 32)
+  int fault_it;            // test hook: stage whose A box is never issued (-1: none)
   unsigned int* err;       // count of bounded waits that ran out
 };
 
@@ -229,7 +230,8 @@ __global__ void __launch_bounds__(kConvThreads, 2)
           // mode 1: one box, tap k0 / Ci, channels k0 % Ci .. + 63; mode 2:
           // taps 2 kt and 2 kt + 1, all 32 channels each (a tap past the
           // ninth is a box far outside the image: zeros)
-          const int nbox = a.tma == 2 ? 2 : 1;
+          // (the test hook leaves one stage's boxes out: its wait runs out)
+          const int nbox = it == a.fault_it ? 0 : (a.tma == 2 ? 2 : 1);
           for (int bx = 0; bx < nbox; ++bx) {
             int tap, c0;
             if (a.tma == 2) {
@@ -558,6 +560,7 @@ struct sil_unet {
   float* head_b = nullptr;
   unsigned int* err = nullptr;
   int last_n = 0;
+  int fault_layer = -1;  // test hook (sil_unet_set_fault)
 };
 
 namespace {
@@ -667,7 +670,8 @@ cudaError_t launch_conv_nt(const ConvArgs& a, const CUtensorMap& tmap, int mtile
 }
 
 cudaError_t run_layer(const Layer& L, int n, unsigned int* err, const float* head_w,
-                      const float* head_b, float* logits, uint8_t* labels, cudaStream_t s) {
+                      const float* head_b, float* logits, uint8_t* labels, bool fault,
+                      cudaStream_t s) {
   ConvArgs a;
   a.x = L.in.base;
   a.xs = L.in.stride;
@@ -690,6 +694,7 @@ cudaError_t run_layer(const Layer& L, int n, unsigned int* err, const float* hea
   a.logits = L.head ? logits : nullptr;
   a.labels = L.head ? labels : nullptr;
   a.tma = L.tma;
+  a.fault_it = (fault && L.tma) ? 0 : -1;
   a.err = err;
   const int mtiles = (a.M + kBM - 1) / kBM, ntiles = L.N / L.NT;
   switch (L.NT) {
@@ -997,12 +1002,23 @@ extern "C" sil_status sil_unet_forward(sil_unet* net, const uint8_t* chips, int3
   // the head is fused into the last decoder convolution, the pooling into
   // the encoders' second convolutions
   for (int i = 0; i < nl - 1 && e == cudaSuccess; ++i)
-    e = run_layer(net->layers[i], n, net->err, net->head_w, net->head_b, logits, labels, s);
+    e = run_layer(net->layers[i], n, net->err, net->head_w, net->head_b, logits, labels,
+                  i == net->fault_layer, s);
   if (e != cudaSuccess) {
     set_error("sil_unet_forward: launch failed: %s", cudaGetErrorString(e));
     return SIL_ECUDA;
   }
   net->last_n = n;
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_set_fault(sil_unet* net, int32_t layer) {
+  if (!net || layer < -1 || layer >= int(net->layers.size()) - 1 ||
+      (layer >= 0 && !net->layers[layer].tma)) {
+    set_error("sil_unet_set_fault: NULL network or layer %d without tensor-map loads", int(layer));
+    return SIL_EINVAL;
+  }
+  net->fault_layer = layer;
   return SIL_OK;
 }
 

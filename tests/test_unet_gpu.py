@@ -127,3 +127,33 @@ def test_unet_rejects_bad_arguments(sil):
         sil.UNet(sil.unet_config(24, 4, 2), wts)  # width not in {16, 32, 64}
     with pytest.raises(ValueError):
         sil.UNet(cfg, wts[:-1])
+
+
+def test_unet_bounded_wait_runs_out_and_recovers(sil):
+    """Failure detection without a GPU fault: the test hook leaves one stage's
+    input load out, so that layer's wait for it runs out (bounded, about
+    1.3 s); the kernel counts the error and returns, and the next forward on
+    the same network and context gives the same scores as before, bit for
+    bit."""
+    F, depth = 16, 2
+    chips = _chips(2, 21)
+    wts = synth.unet_weights(F, depth, seed=3)
+    net, lab0, lg0 = _run(sil, F, depth, chips, wts)
+    assert net.error_count() == 0
+    shapes = sil.unet_layer_shapes(net.cfg)
+    # the first layer with 32 input channels reads by tensor map
+    layer = next(i for i, (s, k) in enumerate(shapes) if k == sil.UNET_CONV3 and s[1] == 32)
+    with pytest.raises(sil.SilError):
+        net.set_fault(0)                 # the first layer gathers: no hook there
+    net.set_fault(layer)
+    dev = torch.from_numpy(chips).cuda()
+    lab = torch.empty(chips.shape[:3], dtype=torch.uint8, device="cuda")
+    lg = torch.empty(chips.shape[:3] + (3,), dtype=torch.float32, device="cuda")
+    net.forward(dev, lab, lg)
+    errors = net.error_count()           # synchronises
+    assert errors > 0
+    net.set_fault(-1)
+    net.forward(dev, lab, lg)
+    torch.cuda.synchronize()
+    assert net.error_count() == errors   # no new errors
+    assert np.array_equal(lg.cpu().numpy(), lg0) and np.array_equal(lab.cpu().numpy(), lab0)
