@@ -67,12 +67,7 @@ sil_status derive_params(const sil_params* p, DevParams* dp) {
   const uint64_t s = uint64_t(p->u16_scale);
   dp->u16_half = uint32_t(s / 2);
   dp->u16_mul = ((uint64_t(1) << 40) + s - 1) / s;
-  dp->one = 1u;
   dp->neg1 = 0xFFFFFFFFu;
-  dp->k8 = 1u << 8;
-  dp->k10 = 1u << 10;
-  dp->k16 = 1u << 16;
-  dp->k24 = 1u << 24;
   // The quotient by multiplication must be exact on every input it meets.
   static thread_local int checked_scale = -1;
   if (checked_scale != p->u16_scale) {

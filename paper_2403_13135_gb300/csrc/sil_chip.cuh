@@ -1,7 +1,7 @@
 // sil_chip.cuh -- the fused per-chip labeler (device code).
 //
-// One CTA of 256 threads labels one chip of at most 256 x 256 pixels; a
-// persistent CTA loops over chips.
+// One CTA of 320 threads (20 half-warps) labels one chip of at most
+// 256 x 256 pixels; a persistent CTA loops over chips.
 //
 //   pass 1  each half-warp owns a band of rows, each lane 16 columns of them.
 //           Rows arrive through a 3-slot shared-memory ring filled by lane-
@@ -92,25 +92,13 @@ __device__ __forceinline__ uint32_t max3(uint32_t a, uint32_t b, uint32_t c) {
 __device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
   return __vimin3_u16x2(a, b, c);
 }
-#ifndef SIL_MED_IMAD
-#define SIL_MED_IMAD 2
-#endif
-#ifndef SIL_P2_IMAD
-#define SIL_P2_IMAD 0
-#endif
 // a * b + c with b a runtime kernel parameter: stays an integer multiply-add,
 // which issues on the multiply-add pipe, beside the min/max/permute pipe.
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) { return a * b + c; }
-// a + b + c - x - y, exact modulo 2^32
+// a + b + c - x - y, exact modulo 2^32 (the two subtractions as multiply-adds)
 __device__ __forceinline__ uint32_t sum3m2(uint32_t a, uint32_t b, uint32_t c, uint32_t x,
                                            uint32_t y, const DevParams& dp) {
-#if SIL_MED_IMAD == 1
-  return imad(y, dp.neg1, imad(x, dp.neg1, imad(c, dp.one, imad(a, dp.one, b))));
-#elif SIL_MED_IMAD == 2
   return imad(y, dp.neg1, imad(x, dp.neg1, a + b + c));
-#else
-  return a + b + c - x - y;
-#endif
 }
 // median of three packed u16x2 words
 __device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c, const DevParams& dp) {
@@ -178,36 +166,6 @@ __device__ __forceinline__ void gather_u8(const uint32_t* v, uint32_t* V, uint32
     V[i] = max3(g[0], g[1], g[2]);
   }
 }
-// u8 from a 16-byte aligned 64-byte window: pixel j is bytes M+3j..M+3j+2
-// (M = 0..15); same pairing as gather_u8.
-template <int M>
-__device__ __forceinline__ void gather_u8w(const uint32_t* v, uint32_t* V, uint32_t (*G)[3]) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    uint32_t g[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int b = M + 3 * i + c;
-      const int wi = b >> 2, p = b & 3;
-      const uint32_t sel = p | (p << 4) | ((4 + p) << 8) | ((4 + p) << 12);
-      g[c] = __byte_perm(v[wi], v[wi + 6], sel);
-      if (G) G[i][c] = g[c];
-    }
-    V[i] = max3(g[0], g[1], g[2]);
-  }
-}
-#define SIL_CASE16(F, ...)                                                 \
-  case 0: F<0>(__VA_ARGS__); break; case 1: F<1>(__VA_ARGS__); break;      \
-  case 2: F<2>(__VA_ARGS__); break; case 3: F<3>(__VA_ARGS__); break;      \
-  case 4: F<4>(__VA_ARGS__); break; case 5: F<5>(__VA_ARGS__); break;      \
-  case 6: F<6>(__VA_ARGS__); break; case 7: F<7>(__VA_ARGS__); break;      \
-  case 8: F<8>(__VA_ARGS__); break; case 9: F<9>(__VA_ARGS__); break;      \
-  case 10: F<10>(__VA_ARGS__); break; case 11: F<11>(__VA_ARGS__); break;  \
-  case 12: F<12>(__VA_ARGS__); break; case 13: F<13>(__VA_ARGS__); break;  \
-  case 14: F<14>(__VA_ARGS__); break; default: F<15>(__VA_ARGS__); break;
-#ifndef SIL_DECODE128
-#define SIL_DECODE128 0
-#endif
 // u16: pixel j is bytes 6j..6j+5 after shift S (even); pair (j, j+8) is 48
 // bytes = 12 words apart at the same half-word position.
 template <int S>
@@ -299,20 +257,7 @@ __device__ __forceinline__ void decode_row(const uint8_t* slot, int m, int q, in
   uint32_t G[8][3];
   constexpr bool kNeedG = HS;
   F[0] = F[1] = 0;
-  if (DT == SIL_U8 && SIL_DECODE128) {
-    // four conflict-free 16-byte reads of the lane's 64-byte window
-    const uint4* w4 = reinterpret_cast<const uint4*>(slot + 48 * q);
-    uint32_t v[16];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint4 t = w4[k];
-      v[4 * k] = t.x;
-      v[4 * k + 1] = t.y;
-      v[4 * k + 2] = t.z;
-      v[4 * k + 3] = t.w;
-    }
-    switch (m) { SIL_CASE16(gather_u8w, v, V, kNeedG ? G : nullptr) }
-  } else if (DT == SIL_U8) {
+  if (DT == SIL_U8) {
     const uint32_t* base = reinterpret_cast<const uint32_t*>(slot) + (m >> 2) + 4 * Px<DT>::BPP * q;
     uint32_t v[NW];
 #pragma unroll
@@ -465,9 +410,6 @@ __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const
 // through its ring of kRing row slots, kRing - 1 rows ahead of the one being
 // decoded.  FULL: every lane has 16 columns (chip width 256).  A4: every row
 // of the chip starts on a 4-byte boundary.
-#ifndef SIL_ROTATE3
-#define SIL_ROTATE3 0
-#endif
 template <int DT, bool HS, bool FULL, bool A4, class SM>
 __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, int64_t y0,
                                            int64_t x0, int h, int w, int r0, int r1,
@@ -521,30 +463,12 @@ __device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, in
   RowBuf M, Z, P;
   step(M);
   step(Z);
-#if SIL_ROTATE3
-  int y = r0;
-  for (; y + 3 <= r1; y += 3) {
-    step(P);
-    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, dp, sm, n_nodata);
-    step(M);
-    emit_row<kFlags, DT, FULL>(Z, P, M, y + 1, q, nvalid, use_median, dp, sm, n_nodata);
-    step(Z);
-    emit_row<kFlags, DT, FULL>(P, M, Z, y + 2, q, nvalid, use_median, dp, sm, n_nodata);
-  }
-  for (; y < r1; ++y) {
-    step(P);
-    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, dp, sm, n_nodata);
-    M = Z;
-    Z = P;
-  }
-#else
   for (int y = r0; y < r1; ++y) {
     step(P);
     emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, dp, sm, n_nodata);
     M = Z;
     Z = P;
   }
-#endif
   wait_rows<0>();
 }
 
@@ -850,18 +774,10 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
     uint32_t l[16];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-#if SIL_P2_IMAD
-      // byte b of a word on the multiply-add pipe: (w << 8 (3 - b)) >> 24
-      l[2 * k] = lut[p[k] & 0xFFu];
-      l[2 * k + 1] = lut[__umulhi(imad(p[k], dp.k16, 0u), dp.k8)];
-      l[2 * k + 8] = lut[__umulhi(imad(p[k], dp.k8, 0u), dp.k8)];
-      l[2 * k + 9] = lut[__umulhi(p[k], dp.k8)];
-#else
       l[2 * k] = lut[__byte_perm(p[k], 0, 0x4440)];
       l[2 * k + 1] = lut[__byte_perm(p[k], 0, 0x4441)];
       l[2 * k + 8] = lut[__byte_perm(p[k], 0, 0x4442)];
       l[2 * k + 9] = lut[__byte_perm(p[k], 0, 0x4443)];
-#endif
     }
     if (kFlags) {
       const uint32_t f0 = sm.flags[y][q][0], f1 = sm.flags[y][q][1];
@@ -884,17 +800,10 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
     }
     if (dst) {
       uint4 lab;
-#if SIL_P2_IMAD
-      lab.x = imad(l[3], dp.k24, imad(l[2], dp.k16, imad(l[1], dp.k8, l[0])));
-      lab.y = imad(l[7], dp.k24, imad(l[6], dp.k16, imad(l[5], dp.k8, l[4])));
-      lab.z = imad(l[11], dp.k24, imad(l[10], dp.k16, imad(l[9], dp.k8, l[8])));
-      lab.w = imad(l[15], dp.k24, imad(l[14], dp.k16, imad(l[13], dp.k8, l[12])));
-#else
       lab.x = __byte_perm(__byte_perm(l[0], l[1], 0x0040), __byte_perm(l[2], l[3], 0x0040), 0x5410);
       lab.y = __byte_perm(__byte_perm(l[4], l[5], 0x0040), __byte_perm(l[6], l[7], 0x0040), 0x5410);
       lab.z = __byte_perm(__byte_perm(l[8], l[9], 0x0040), __byte_perm(l[10], l[11], 0x0040), 0x5410);
       lab.w = __byte_perm(__byte_perm(l[12], l[13], 0x0040), __byte_perm(l[14], l[15], 0x0040), 0x5410);
-#endif
       store_row16(dst, nvalid, lab);
       dst += lpitch;
     }

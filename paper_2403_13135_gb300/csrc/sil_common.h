@@ -16,10 +16,9 @@ struct DevParams {
   int32_t need_hs;        // 1 if some class range narrows H or S
   uint64_t u16_mul;       // ceil(2^40 / u16_scale): n / s == (n * mul) >> 40
   uint32_t u16_half;      // u16_scale / 2
-  // Multipliers 1, -1, 2^8, 2^10, 2^16, 2^24.  Read from the kernel
-  // parameters so that sums and byte moves stay integer multiply-adds, which
-  // issue on a different pipe than min/max and byte permutes.
-  uint32_t one, neg1, k8, k10, k16, k24;
+  // -1, read from the kernel parameters so that the median's subtractions
+  // stay integer multiply-adds, which issue on a different pipe than min/max.
+  uint32_t neg1;
 };
 
 // One labelling request (a tile or a whole scene) as the kernels see it.
