@@ -144,8 +144,9 @@ __device__ __forceinline__ void wait_rows() { asm volatile("cp.async.wait_group 
 // ---------------------------------------------------------------------------
 // Decode of a lane's 16 pixels from a staged row.  The lane's bytes start at
 // slot offset m + 16 BPP q; the words are read from the aligned word below
-// and the byte shift s = m & 3 (the same for all lanes) picks one of four
-// gathers.
+// and, unless m & 3 == 0, funnel-shifted by 8 (m & 3) bits (the same shift
+// for all lanes of the half-warp) so that the gathers below see the row's
+// first byte at byte 0 (S = 0).
 // ---------------------------------------------------------------------------
 // u8: pixel j is bytes 3j..3j+2 after shift S; pair (j, j+8) is 24 bytes = 6
 // words apart at the same byte position, so one PRMT lifts both channel bytes
@@ -244,12 +245,7 @@ struct Px {
 // at byte m of the slot) into 8 interleaved V words; F[0], F[1] = per-pixel
 // flags of columns 0-7 / 8-15 (nibble: bits 0-2 H/S class mask, bit 3
 // nodata) for the variants that need them.  A4: every row of the chip starts
-// on a 4-byte boundary (m & 3 == 0), so the byte-shift dispatch, whose case
-// can differ between the two half-warps of a warp, is left out.
-#define SIL_CASE4(F, ...)                                         \
-  case 0: F<0>(__VA_ARGS__); break; case 1: F<1>(__VA_ARGS__); break; \
-  case 2: F<2>(__VA_ARGS__); break; default: F<3>(__VA_ARGS__); break;
-
+// on a 4-byte boundary (m & 3 == 0), so the realigning shift is left out.
 template <int DT, bool HS, bool A4>
 __device__ __forceinline__ void decode_row(const uint8_t* slot, int m, int q, int nvalid,
                                            const DevParams& dp, uint32_t* V, uint32_t* F) {
@@ -262,20 +258,27 @@ __device__ __forceinline__ void decode_row(const uint8_t* slot, int m, int q, in
     uint32_t v[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) v[k] = base[k];
-    if (A4)
-      gather_u8<0>(v, V, kNeedG ? G : nullptr);
-    else
-      switch (m & 3) { SIL_CASE4(gather_u8, v, V, kNeedG ? G : nullptr) }
+    if (!A4) {
+      // realign to the row's first byte: one funnel shift per word, the same
+      // for every lane (no per-case code, no divergence between the two
+      // half-warps of a warp, whose rows can start at different offsets)
+      const uint32_t sh = 8u * uint32_t(m & 3);
+#pragma unroll
+      for (int k = 0; k < NW - 1; ++k) v[k] = __funnelshift_r(v[k], v[k + 1], sh);
+    }
+    gather_u8<0>(v, V, kNeedG ? G : nullptr);
   } else {
     const uint32_t* base = reinterpret_cast<const uint32_t*>(slot) + (m >> 2) + 4 * Px<DT>::BPP * q;
     uint32_t v[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) v[k] = base[k];
     uint32_t R[8];
-    if (!A4 && (m & 2))
-      gather_u16<2>(v, R, kNeedG ? G : nullptr);
-    else
-      gather_u16<0>(v, R, kNeedG ? G : nullptr);
+    if (!A4) {
+      const uint32_t sh = 8u * uint32_t(m & 2);
+#pragma unroll
+      for (int k = 0; k < NW - 1; ++k) v[k] = __funnelshift_r(v[k], v[k + 1], sh);
+    }
+    gather_u16<0>(v, R, kNeedG ? G : nullptr);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const uint32_t x0 = R[i] & 0xFFFFu, x1 = R[i] >> 16;
