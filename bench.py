@@ -366,7 +366,7 @@ def run_sil(args):
                          "avg_launch_us": avg_launch * 1e6},
             "clocks": clocks,
         }
-        if not args.no_cpu_baseline and ws >= 1:
+        if not args.no_cpu_baseline and ws == 1:  # rank 0 at N = 1 only
             pool = OraclePool(img, args.cpu_cores or None)
             try:
                 v, sample = pool.run(args.cpu_budget)
