@@ -74,9 +74,9 @@ def _ulp_bf16(v):
     return np.ldexp(1.0, e - 8)
 
 
-@pytest.mark.parametrize("F,depth", [(16, 2), (32, 4)])
-def test_unet_layers_against_oracle(sil, F, depth):
-    chips = _chips(2, 11 + F)
+@pytest.mark.parametrize("F,depth,n", [(16, 2, 2), (32, 4, 2), (64, 3, 1)])
+def test_unet_layers_against_oracle(sil, F, depth, n):
+    chips = _chips(n, 11 + F)
     wts = synth.unet_weights(F, depth, seed=F)
     net, lab, lg = _run(sil, F, depth, chips, wts)
     outs, ref_lg, ref_lab = _oracle_chain(chips, wts, depth)
