@@ -18,6 +18,7 @@ median3x3(V)                -> 3x3 median of a 2-D uint8 array, clamped border
 otsu(hist, fallback)        -> Otsu threshold of a 256-bin histogram
 stretch(v, lo, hi)          -> min-max normalised value
 label(img, params, ...)     -> (labels, counts, chip_counts, chip_stats)
+filtered_value(img, params) -> V' plane (the filter's corrected value)
 confusion(pred, ref, chip)  -> (conf[4][4], chip_conf[gy][gx][4][4])
 """
 from __future__ import annotations
@@ -94,6 +95,11 @@ def _load():
         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
         ctypes.POINTER(OracleParams), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
         ctypes.c_void_p, ctypes.c_void_p]
+    lib.sil_oracle_label_v.argtypes = [
+        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+        ctypes.POINTER(OracleParams), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.sil_oracle_label_v.restype = ctypes.c_int
     lib.sil_oracle_confusion.argtypes = [
         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
         ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
@@ -198,6 +204,26 @@ def label(img: np.ndarray, params: dict | None = None, *, pitch: int | None = No
         raise ValueError("sil_oracle_label: invalid arguments")
     st = [{f: getattr(s, f) for f in ("n", "lo", "hi", "t", "n0", "n1", "gate")} for s in stats]
     return labels, counts, chip_counts, st
+
+
+def filtered_value(img: np.ndarray, params: dict | None = None) -> np.ndarray:
+    """The filter's corrected value V' of every pixel of an H x W x 3 uint8 or
+    uint16 image (the value the class ranges are applied to: V after the
+    median, the gated min-max stretch and the truncation; V itself when the
+    filter is off; 0 for nodata), H x W uint8."""
+    lib = _load()
+    p = _from_dict(params)
+    assert img.ndim == 3 and img.shape[2] == 3 and img.dtype in (np.uint8, np.uint16)
+    H, W = img.shape[0], img.shape[1]
+    buf = np.ascontiguousarray(img)
+    vp = np.empty((H, W), np.uint8)
+    counts = np.zeros(4, np.uint64)
+    rc = lib.sil_oracle_label_v(buf.ctypes.data, H, W, buf.strides[0], 0 if img.dtype == np.uint8 else 1,
+                                ctypes.byref(p), None, W, vp.ctypes.data, W, counts.ctypes.data,
+                                None, None)
+    if rc != 0:
+        raise ValueError("sil_oracle_label_v: invalid arguments")
+    return vp
 
 
 def confusion(pred: np.ndarray, ref: np.ndarray, chip: int = 256):

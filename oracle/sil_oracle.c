@@ -247,13 +247,17 @@ static void read_pixel(const uint8_t* img, int64_t pitch, int dtype, int64_t y,
 /* The whole path on one request (Sec. III-B filter + auto-labeling, and the
  * map-reduce count).  img: H x W x 3 (uint8 or uint16), pitch bytes per row.
  * labels: H x W uint8 with label_pitch bytes per row (may be NULL).
+ * vprime: H x W uint8 with vprime_pitch bytes per row (may be NULL): the
+ * filter's corrected value V' of every pixel (V when the filter is off, 0 for
+ * nodata), the value the class ranges are applied to.
  * counts: uint64[4] (overwritten).  chip_counts: uint32[ceil(H/C)][ceil(W/C)][4]
  * (may be NULL).  stats: one entry per chip, same order (may be NULL).
  * Returns 0, or 1 for invalid arguments. */
-int sil_oracle_label(const void* img_v, int64_t H, int64_t W, int64_t pitch,
-                     int dtype, const sil_oracle_params* p, uint8_t* labels,
-                     int64_t label_pitch, uint64_t* counts,
-                     uint32_t* chip_counts, sil_oracle_chip_stats* stats) {
+int sil_oracle_label_v(const void* img_v, int64_t H, int64_t W, int64_t pitch,
+                       int dtype, const sil_oracle_params* p, uint8_t* labels,
+                       int64_t label_pitch, uint8_t* vprime_out, int64_t vprime_pitch,
+                       uint64_t* counts, uint32_t* chip_counts,
+                       sil_oracle_chip_stats* stats) {
   const uint8_t* img = (const uint8_t*)img_v;
   if (!img || !p || !counts || H < 1 || W < 1) return ORC_EINVAL;
   if (dtype != 0 && dtype != 1) return ORC_EINVAL;
@@ -261,6 +265,7 @@ int sil_oracle_label(const void* img_v, int64_t H, int64_t W, int64_t pitch,
   int bpp = dtype == 0 ? 3 : 6;
   if (pitch < W * bpp) return ORC_EINVAL;
   if (labels && label_pitch < W) return ORC_EINVAL;
+  if (vprime_out && vprime_pitch < W) return ORC_EINVAL;
 
   const int C = p->chip;
   const int64_t gy = (H + C - 1) / C, gx = (W + C - 1) / C;
@@ -353,6 +358,8 @@ int sil_oracle_label(const void* img_v, int64_t H, int64_t W, int64_t pitch,
           /* Step 8: map-reduce counts. */
           cc[label] += 1;
           if (labels) labels[(y0 + y) * label_pitch + (x0 + x)] = (uint8_t)label;
+          if (vprime_out)
+            vprime_out[(y0 + y) * vprime_pitch + (x0 + x)] = (uint8_t)(ND[i] ? 0 : vprime);
         }
       }
       for (int k = 0; k < 4; ++k) counts[k] += cc[k];
@@ -362,6 +369,14 @@ int sil_oracle_label(const void* img_v, int64_t H, int64_t W, int64_t pitch,
   }
   free(Hc); free(Sc); free(Vc); free(Vf); free(ND);
   return ORC_OK;
+}
+
+int sil_oracle_label(const void* img_v, int64_t H, int64_t W, int64_t pitch,
+                     int dtype, const sil_oracle_params* p, uint8_t* labels,
+                     int64_t label_pitch, uint64_t* counts,
+                     uint32_t* chip_counts, sil_oracle_chip_stats* stats) {
+  return sil_oracle_label_v(img_v, H, W, pitch, dtype, p, labels, label_pitch, NULL, 0, counts,
+                            chip_counts, stats);
 }
 
 /* Confusion counts of one label map against a reference map (Sec. IV-A,

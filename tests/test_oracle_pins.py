@@ -385,3 +385,37 @@ def test_confusion_matches_bincount():
     np.testing.assert_array_equal(chip_conf.sum(axis=(0, 1)), conf)
     sub = np.bincount((a[32:64, 64:90].astype(int) * 4 + b[32:64, 64:90]).ravel(), minlength=16)
     np.testing.assert_array_equal(chip_conf[1, 2].ravel(), sub)
+
+
+# --------------------------------------------------------------------------
+# The filter's corrected value V' (the U-Net's filtered input is built from it).
+# --------------------------------------------------------------------------
+def test_vprime_is_v_without_filter():
+    img, _ = synth.scene(130, 170, 4, n_floes=5)
+    vp = oracle.filtered_value(img, {"filter": 0})
+    assert np.array_equal(vp, img.max(axis=2))
+
+
+def test_vprime_worked_example_endpoints():
+    """Ex1 of the hand-labelled tiles: lo = 60 stretches to 0, hi = 180 to 255
+    (min-max normalisation, Sec. III-B)."""
+    case = next(c for c in _golden_cases() if c["name"] == "ex1_two_levels_stretched")
+    vp = oracle.filtered_value(_grey(case["v"]), case["params"])
+    assert np.array_equal(vp, np.array([[0, 0, 255, 255]] * 4, np.uint8))
+
+
+def test_vprime_decides_the_class():
+    """With the default ranges (H and S unconstrained) and no absdiff mask, a
+    pixel's label is the class whose V range holds its V'."""
+    img, _ = synth.scene(400, 300, 6, n_floes=9, n_haze=2, n_shadow=2)
+    labels, _, _, _ = oracle.label(img)
+    vp = oracle.filtered_value(img)
+    expect = np.where(vp >= 205, 0, np.where(vp >= 31, 1, 2)).astype(np.uint8)
+    assert np.array_equal(labels, expect)
+
+
+def test_vprime_nodata_is_zero():
+    img, _ = synth.scene(200, 260, 8, n_floes=4, dtype=np.uint16)
+    vp = oracle.filtered_value(img)
+    nodata = (img == 0).all(axis=2)
+    assert nodata.any() and not vp[nodata].any()
