@@ -9,7 +9,11 @@ following the encoder-decoder of Sec. III-C "U-Net Model Inferencing"
 Model Training" (a U-Net).  The paper fixes neither the widths nor the
 precision, so the readings are:
 
-* input: the chip's R, G, B bytes scaled by 1/256 (exact in bfloat16);
+* input: the chip's R, G, B bytes scaled by 1/256 (exact in bfloat16); the
+  filtered input (Sec. III-C feeds the filtered image to the U-Net) first
+  scales each pixel's R, G, B by V'/V, V = max(R, G, B) and V' the filter's
+  corrected value (HSV with V replaced, H and S kept), rounded half up to an
+  integer: c' = floor((2 c V' + V) / (2 V)), 0 when V = 0;
 * encoder: 4 levels of two 3x3 convolutions (zero padding 1, bias, ReLU)
   followed by 2x2 max pooling; widths F, 2F, 4F, 8F; a bottleneck of two
   3x3 convolutions of width 16F;
@@ -44,6 +48,16 @@ def bf16(x: np.ndarray) -> np.ndarray:
 def prep(chips_u8: np.ndarray) -> np.ndarray:
     """[B, 256, 256, 3] uint8 -> [B, 256, 256, 3] float64 activations v / 256."""
     return np.asarray(chips_u8, dtype=np.float64) / 256.0
+
+
+def prep_filtered(chips_u8: np.ndarray, vprime_u8: np.ndarray) -> np.ndarray:
+    """[B, 256, 256, 3] uint8 chips and their [B, 256, 256] V' -> the filtered
+    chips' activations c' / 256, c' = floor((2 c V' + V) / (2 V)) (0 if V = 0)."""
+    c = np.asarray(chips_u8, dtype=np.int64)
+    v = c.max(axis=-1, keepdims=True)
+    vp = np.asarray(vprime_u8, dtype=np.int64)[..., None]
+    cf = np.where(v > 0, (2 * c * vp + v) // np.maximum(2 * v, 1), 0)
+    return cf.astype(np.float64) / 256.0
 
 
 def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray, relu: bool = True) -> np.ndarray:
@@ -93,12 +107,13 @@ def head(x: np.ndarray, w: np.ndarray, b: np.ndarray):
     return logits, np.argmax(logits, axis=-1).astype(np.uint8)
 
 
-def forward(chips_u8: np.ndarray, weights: dict, depth: int = 4):
-    """The whole network on [B, 256, 256, 3] uint8 chips.
+def forward(chips_u8: np.ndarray, weights: dict, depth: int = 4, vprime_u8=None):
+    """The whole network on [B, 256, 256, 3] uint8 chips (filtered by their
+    [B, 256, 256] V' when vprime_u8 is given).
     weights: 'enc{l}_{0,1}' / 'bott_{0,1}' / 'dec{l}_{0,1}' conv (w, b),
     'up{l}' transposed conv (w, b), 'head' (w, b).
     Returns (logits [B, H, W, 3] float32, labels [B, H, W] uint8)."""
-    x = prep(chips_u8)
+    x = prep(chips_u8) if vprime_u8 is None else prep_filtered(chips_u8, vprime_u8)
     skips = []
     for lvl in range(depth):
         x = conv3x3(x, *weights[f"enc{lvl}_0"])

@@ -128,3 +128,27 @@ def test_weights_exact_in_bf16():
     for name, (w, b) in synth.unet_weights(8, 4, 1).items():
         assert np.array_equal(U.bf16(w.astype(np.float64)), w), name
         assert np.array_equal(U.bf16(b.astype(np.float64)), b), name
+
+
+def test_prep_filtered_closed_forms():
+    """V' = V leaves the chip unchanged; V' = 0 gives black; V' = 2V doubles
+    grey pixels; every c' <= V' and the largest channel becomes V'."""
+    rng = np.random.default_rng(9)
+    chips = rng.integers(0, 256, (1, 256, 256, 3)).astype(np.uint8)
+    v = chips.max(axis=-1)
+    assert np.array_equal(U.prep_filtered(chips, v), U.prep(chips))
+    assert not U.prep_filtered(chips, np.zeros_like(v)).any()
+    grey = np.repeat(rng.integers(0, 128, (1, 256, 256, 1)).astype(np.uint8), 3, axis=-1)
+    got = U.prep_filtered(grey, (2 * grey[..., 0]).astype(np.uint8))
+    assert np.array_equal(got, 2 * U.prep(grey))
+    vp = rng.integers(0, 256, v.shape).astype(np.uint8)
+    cf = np.round(U.prep_filtered(chips, vp) * 256).astype(np.int64)
+    assert (cf <= vp[..., None]).all()
+    assert np.array_equal(cf.max(axis=-1)[v > 0], vp[v > 0])
+    # brute force on a few pixels, exact fractions
+    from fractions import Fraction
+    for (y, x) in [(0, 0), (17, 200), (255, 255), (128, 3)]:
+        for c in range(3):
+            V = int(v[0, y, x])
+            want = 0 if V == 0 else int(Fraction(int(chips[0, y, x, c]) * int(vp[0, y, x]), V) + Fraction(1, 2))
+            assert cf[0, y, x, c] == want
