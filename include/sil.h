@@ -129,6 +129,18 @@ sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
                      int64_t label_pitch, uint64_t* counts,
                      uint32_t* chip_counts, sil_stream stream);
 
+/* sil_label plus the filter's corrected value: vprime = DEVICE uint8 H x W
+ * with vprime_pitch bytes per row (NULL: none) receives V' of every pixel,
+ * the value the class ranges are applied to (Sec. III-B): V after the 3x3
+ * median, the gated min-max stretch and the truncation; V when the filter is
+ * off; 0 for nodata.  Scaling a pixel's R, G, B by V'/V gives the filtered
+ * image the paper feeds to its U-Net (Sec. III-C; see
+ * sil_unet_forward_filtered).  SIL_EINVAL also when vprime_pitch < W. */
+sil_status sil_label_v(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
+                       sil_dtype dt, const sil_params* p, uint8_t* labels,
+                       int64_t label_pitch, uint8_t* vprime, int64_t vprime_pitch,
+                       uint64_t* counts, uint32_t* chip_counts, sil_stream stream);
+
 /* Same as sil_label but the image, labels and counts are HOST buffers; the
  * library stages them through its own device buffers and returns when the
  * results are in host memory.  The image is cut into stripes of whole chip

@@ -21,6 +21,9 @@
  *            the largest score, the first on ties (0 thick ice, 1 thin ice,
  *            2 open water)
  *
+ * The input may be the filtered chip (sil_unet_forward_filtered), as in the
+ * paper's workflow.
+ *
  * Every activation is stored as bfloat16 (round to nearest even) in
  * channels-last layout; products are bfloat16 x bfloat16 summed in float32
  * on the tensor cores.
@@ -92,6 +95,16 @@ void sil_unet_destroy(sil_unet* net);
  * sil_unet_error_count reports. */
 sil_status sil_unet_forward(sil_unet* net, const uint8_t* chips, int32_t n, uint8_t* labels,
                             float* logits, sil_stream stream);
+
+/* The same on the filtered chips, as the paper's inferencing workflow does
+ * (Sec. III-C): vprime = DEVICE uint8 [n][256][256], the filter's corrected
+ * value V' of every pixel (sil_label_v on the scene, cut like the chips);
+ * each pixel's R, G, B is first scaled by V'/V, V = max(R, G, B), rounded half
+ * up: c' = floor((2 c V' + V) / (2 V)), 0 when V = 0 (HSV with V replaced by
+ * V', H and S kept).  vprime = NULL is sil_unet_forward. */
+sil_status sil_unet_forward_filtered(sil_unet* net, const uint8_t* chips, const uint8_t* vprime,
+                                     int32_t n, uint8_t* labels, float* logits,
+                                     sil_stream stream);
 
 /* Synchronises the device and returns the number of kernel waits that ran
  * out since the network was created (0 in normal operation). */

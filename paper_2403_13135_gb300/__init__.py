@@ -88,6 +88,8 @@ _SIGS = {
     "sil_version": ([], ctypes.c_int),
     "sil_label": ([_P, _I64, _I64, _I64, _I32, ctypes.POINTER(sil_params), _P, _I64, _P, _P, _P], _I32),
     "sil_label_host": ([_P, _I64, _I64, _I64, _I32, ctypes.POINTER(sil_params), _P, _I64, _P, _P, _P], _I32),
+    "sil_label_v": ([_P, _I64, _I64, _I64, _I32, ctypes.POINTER(sil_params), _P, _I64, _P, _I64, _P, _P,
+                     _P], _I32),
     "sil_ctx_create": ([ctypes.POINTER(_P), _I32], _I32),
     "sil_ctx_destroy": ([_P], None),
     "sil_label_batch": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P, _P], _I32),
@@ -112,6 +114,7 @@ _SIGS = {
                          ctypes.POINTER(ctypes.POINTER(ctypes.c_float)), _I32], _I32),
     "sil_unet_destroy": ([_P], None),
     "sil_unet_forward": ([_P, _P, _I32, _P, _P, _P], _I32),
+    "sil_unet_forward_filtered": ([_P, _P, _P, _I32, _P, _P, _P], _I32),
     "sil_unet_error_count": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I32),
     "sil_unet_set_fault": ([_P, _I32], _I32),
     "sil_unet_tensor_shape": ([_P, _I32, ctypes.POINTER(_I64)], _I32),
@@ -209,6 +212,22 @@ def label(img, p=None, *, labels=True, chip_counts=False, out_labels=None,
                          cnt.data_ptr(), cc.data_ptr() if cc is not None else None,
                          _stream_handle(stream)))
     return lab, cnt, cc
+
+
+def label_v(img, p=None, *, labels=True, stream=None):
+    """Like ``label`` plus the filter's corrected value V' of every pixel
+    (uint8 H x W; sil_label_v).  Returns (labels or None, vprime, counts)."""
+    import torch
+    H, W, pitch, dt = _img_geometry(img)
+    pp = _as_params(p)
+    dev = img.device
+    lab = torch.empty((H, W), dtype=torch.uint8, device=dev) if labels else None
+    vp = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    cnt = torch.empty(4, dtype=torch.int64, device=dev)
+    check(_lib.sil_label_v(img.data_ptr(), H, W, pitch, dt, ctypes.byref(pp),
+                           lab.data_ptr() if lab is not None else None, W, vp.data_ptr(), W,
+                           cnt.data_ptr(), None, _stream_handle(stream)))
+    return lab, vp, cnt
 
 
 def label_host(img: np.ndarray, p=None, *, labels=True, chip_counts=False, stream=None):
@@ -447,14 +466,16 @@ class UNet:
     def flops_per_chip(self) -> int:
         return int(_lib.sil_unet_flops_per_chip(ctypes.byref(self.cfg)))
 
-    def forward(self, chips, labels=None, logits=None, stream=None):
+    def forward(self, chips, labels=None, logits=None, stream=None, vprime=None):
         """chips: cuda uint8 [n, 256, 256, 3]; labels: cuda uint8 [n, 256, 256]
-        or None; logits: cuda float32 [n, 256, 256, 3] or None."""
+        or None; logits: cuda float32 [n, 256, 256, 3] or None; vprime: cuda
+        uint8 [n, 256, 256] (the filter's V') to run on the filtered chips."""
         n = int(chips.shape[0])
-        check(_lib.sil_unet_forward(self.handle, chips.data_ptr(), n,
-                                    labels.data_ptr() if labels is not None else None,
-                                    logits.data_ptr() if logits is not None else None,
-                                    _stream_handle(stream)))
+        check(_lib.sil_unet_forward_filtered(self.handle, chips.data_ptr(),
+                                             vprime.data_ptr() if vprime is not None else None, n,
+                                             labels.data_ptr() if labels is not None else None,
+                                             logits.data_ptr() if logits is not None else None,
+                                             _stream_handle(stream)))
 
     def set_fault(self, layer: int) -> None:
         """Test hook: make layer `layer`'s bounded wait run out (-1 clears)."""

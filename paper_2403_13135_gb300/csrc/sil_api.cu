@@ -96,11 +96,12 @@ __global__ void __launch_bounds__(kThreads, (DT == SIL_U8) ? 2 : 1)
     k_label(Req r, DevParams dp, int chip) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   __shared__ uint8_t lut[256];
+  __shared__ uint8_t vlut[256];
   ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
   const int64_t nchips = int64_t(r.gx) * r.gy;
   for (int64_t k = blockIdx.x; k < nchips; k += gridDim.x) {
     const int64_t cy = k / r.gx, cx = k - cy * r.gx;
-    label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut);
+    label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, vlut);
   }
 }
 
@@ -305,9 +306,21 @@ sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
                      sil_dtype dt, const sil_params* p, uint8_t* labels,
                      int64_t label_pitch, uint64_t* counts, uint32_t* chip_counts,
                      sil_stream stream) {
+  return sil_label_v(img, H, W, pitch_bytes, dt, p, labels, label_pitch, nullptr, 0, counts,
+                     chip_counts, stream);
+}
+
+sil_status sil_label_v(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
+                       sil_dtype dt, const sil_params* p, uint8_t* labels,
+                       int64_t label_pitch, uint8_t* vprime, int64_t vprime_pitch,
+                       uint64_t* counts, uint32_t* chip_counts, sil_stream stream) {
   g_err[0] = 0;
   sil_status st = check_request(img, H, W, pitch_bytes, dt, labels, label_pitch, counts);
   if (st != SIL_OK) return st;
+  if (vprime && vprime_pitch < W) {
+    set_error("sil_label_v: vprime_pitch %lld < W %lld", (long long)vprime_pitch, (long long)W);
+    return SIL_EINVAL;
+  }
   DevParams dp;
   st = derive_params(p, &dp);
   if (st != SIL_OK) return st;
@@ -324,6 +337,8 @@ sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
   r.gx = int32_t((W + chip - 1) / chip);
   r.gy = int32_t((H + chip - 1) / chip);
   r.chip_begin = 0;
+  r.vprime = vprime;
+  r.vpitch = vprime_pitch;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(uint64_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "sil_label: memset counts");

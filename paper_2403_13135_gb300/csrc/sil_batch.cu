@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kThreads, (DT == SIL_U8) ? 2 : 1)
     const int64_t cy = local / r.gx, cx = local - cy * r.gx;
     if (RESIDENT) {
       ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
-      label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut);
+      label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, lut);  // (batches have no V' output)
     } else {
       label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st_generic, lut);
     }

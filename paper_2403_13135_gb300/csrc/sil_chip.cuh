@@ -710,12 +710,9 @@ __device__ __forceinline__ void chip_stats_block(ChipStat& st, StatScratch& sc,
   __syncthreads();
 }
 
-// Label table entry for filtered value vf (thread per value).
-// Non-H/S variant: the label code.  H/S variant: bits 0-2 = classes whose V
-// range holds V', bit 3 = absdiff override.
-template <bool HS>
-__device__ __forceinline__ uint32_t lut_entry(int vf, const ChipStat& sm,
-                                              const DevParams& dp) {
+// V' of filtered value vf: the gated min-max stretch (round half up) and the
+// truncation (Sec. III-B); vf itself when the filter is off.
+__device__ __forceinline__ int vprime_value(int vf, const ChipStat& sm, const DevParams& dp) {
   int vp = vf;
   if (dp.filter) {
     const int lo = sm.stat[kStatLo], hi = sm.stat[kStatHi];
@@ -726,6 +723,16 @@ __device__ __forceinline__ uint32_t lut_entry(int vf, const ChipStat& sm,
     }
     vp = min(vp, dp.v_trunc);
   }
+  return vp;
+}
+
+// Label table entry for filtered value vf (thread per value).
+// Non-H/S variant: the label code.  H/S variant: bits 0-2 = classes whose V
+// range holds V', bit 3 = absdiff override.
+template <bool HS>
+__device__ __forceinline__ uint32_t lut_entry(int vf, const ChipStat& sm,
+                                              const DevParams& dp) {
+  const int vp = vprime_value(vf, sm, dp);
   uint32_t vm = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -813,12 +820,49 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
   }
 }
 
+// Optional output of the filter's corrected value: V' = vlut[Vf] per pixel
+// (0 for nodata), rows r0..r1-1 of the band.
+template <bool kFlags, class SM>
+__device__ __forceinline__ void band_vprime(uint8_t* out, int64_t pitch, int64_t y0, int64_t x0,
+                                            int w, int r0, int r1, const uint8_t* vlut,
+                                            const SM& sm) {
+  const int q = threadIdx.x & 15;
+  const int nvalid = min(max(w - 16 * q, 0), 16);
+  if (nvalid == 0) return;
+  uint8_t* dst = out + (y0 + r0) * pitch + x0 + 16 * q;
+  for (int y = r0; y < r1; ++y, dst += pitch) {
+    const uint4 pw = *reinterpret_cast<const uint4*>(&sm.vf[y * kPlaneStride + 16 * q]);
+    const uint32_t p[4] = {pw.x, pw.y, pw.z, pw.w};
+    uint32_t l[16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      l[2 * k] = vlut[__byte_perm(p[k], 0, 0x4440)];
+      l[2 * k + 1] = vlut[__byte_perm(p[k], 0, 0x4441)];
+      l[2 * k + 8] = vlut[__byte_perm(p[k], 0, 0x4442)];
+      l[2 * k + 9] = vlut[__byte_perm(p[k], 0, 0x4443)];
+    }
+    if (kFlags) {
+      const uint32_t f0 = sm.flags[y][q][0], f1 = sm.flags[y][q][1];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if ((((j < 8 ? f0 : f1) >> (4 * (j & 7))) & 8u) != 0) l[j] = 0;
+    }
+    uint4 v;
+    v.x = __byte_perm(__byte_perm(l[0], l[1], 0x0040), __byte_perm(l[2], l[3], 0x0040), 0x5410);
+    v.y = __byte_perm(__byte_perm(l[4], l[5], 0x0040), __byte_perm(l[6], l[7], 0x0040), 0x5410);
+    v.z = __byte_perm(__byte_perm(l[8], l[9], 0x0040), __byte_perm(l[10], l[11], 0x0040), 0x5410);
+    v.w = __byte_perm(__byte_perm(l[12], l[13], 0x0040), __byte_perm(l[14], l[15], 0x0040), 0x5410);
+    store_row16(dst, nvalid, v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The whole chip.  All threads of the CTA must call it.
 // ---------------------------------------------------------------------------
 template <int DT, bool HS, class SM>
 __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, int chip,
-                                           int64_t cy, int64_t cx, SM& sm, uint8_t* lut) {
+                                           int64_t cy, int64_t cx, SM& sm, uint8_t* lut,
+                                           uint8_t* vlut) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, band = tid >> 4;
   const int64_t y0 = cy * chip, x0 = cx * chip;
   const int h = int(min(int64_t(chip), r.H - y0));
@@ -863,6 +907,7 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
   if (tid < 256) {
     e = lut_entry<HS>(tid, sm.st, dp);
     lut[tid] = uint8_t(e);
+    if (r.vprime) vlut[tid] = uint8_t(vprime_value(tid, sm.st, dp));
   }
   if (!HS && tid < 256) {
     // counts = histogram x label table (nodata pixels are added below)
@@ -897,6 +942,8 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
   } else if (r0 < r1 && (HS || r.labels)) {
     band_pass2<DT, HS>(r.labels, r.lpitch, y0, x0, w, r0, r1, lut, sm, cnt, dp);
   }
+  if (r.vprime && r0 < r1)
+    band_vprime<HS || DT == SIL_U16>(r.vprime, r.vpitch, y0, x0, w, r0, r1, vlut, sm);
   if (HS) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {

@@ -31,6 +31,8 @@ struct Req {
   uint32_t* chip_counts;  // may be null
   int32_t gx, gy;         // chip grid
   int64_t chip_begin;     // index of this request's first chip in a batch
+  uint8_t* vprime = nullptr;  // optional: the filter's corrected value V' per pixel
+  int64_t vpitch = 0;
 };
 
 #ifndef SIL_THREADS

@@ -122,6 +122,7 @@ __device__ void label_chip_generic(const Req& r, const DevParams& dp, int chip,
     if (nd) lab = 3u;
     cnt[lab] += 1;
     if (r.labels) r.labels[(y0 + y) * r.lpitch + x0 + x] = uint8_t(lab);
+    if (r.vprime) r.vprime[(y0 + y) * r.vpitch + x0 + x] = nd ? 0 : uint8_t(vprime_value(vf, sm, dp));
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {

@@ -524,6 +524,24 @@ __global__ void k_prep(const uint8_t* __restrict__ chips, int64_t P, __nv_bfloat
                                               *reinterpret_cast<const uint32_t*>(&b0), 0u, 0u);
 }
 
+// The filtered chip (Sec. III-C): each pixel's R, G, B scaled by V'/V, V the
+// largest of them and V' the filter's corrected value, rounded half up
+// (c' = floor((2 c V' + V) / (2 V)), 0 when V = 0), then / 256 as k_prep.
+__global__ void k_prep_filtered(const uint8_t* __restrict__ chips, const uint8_t* __restrict__ vprime,
+                                int64_t P, __nv_bfloat16* __restrict__ x) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const uint8_t* s = chips + 3 * p;
+  const int v = max(int(s[0]), max(int(s[1]), int(s[2]))), vp = vprime[p];
+  float f[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f[c] = v ? float((2 * int(s[c]) * vp + v) / (2 * v)) * (1.f / 256.f) : 0.f;
+  const __nv_bfloat162 rg = __floats2bfloat162_rn(f[0], f[1]);
+  const __nv_bfloat162 b0 = __floats2bfloat162_rn(f[2], 0.f);
+  reinterpret_cast<uint4*>(x)[p] = make_uint4(*reinterpret_cast<const uint32_t*>(&rg),
+                                              *reinterpret_cast<const uint32_t*>(&b0), 0u, 0u);
+}
+
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
@@ -990,13 +1008,22 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
 
 extern "C" sil_status sil_unet_forward(sil_unet* net, const uint8_t* chips, int32_t n,
                                        uint8_t* labels, float* logits, sil_stream stream) {
+  return sil_unet_forward_filtered(net, chips, nullptr, n, labels, logits, stream);
+}
+
+extern "C" sil_status sil_unet_forward_filtered(sil_unet* net, const uint8_t* chips,
+                                                const uint8_t* vprime, int32_t n, uint8_t* labels,
+                                                float* logits, sil_stream stream) {
   if (!net || !chips || n < 1 || n > net->cfg.max_batch) {
     set_error("sil_unet_forward: NULL network/chips or n=%d outside 1..max_batch", int(n));
     return SIL_EINVAL;
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t P = int64_t(n) * kChip * kChip;
-  k_prep<<<unsigned((P + 255) / 256), 256, 0, s>>>(chips, P, net->x0);
+  if (vprime)
+    k_prep_filtered<<<unsigned((P + 255) / 256), 256, 0, s>>>(chips, vprime, P, net->x0);
+  else
+    k_prep<<<unsigned((P + 255) / 256), 256, 0, s>>>(chips, P, net->x0);
   cudaError_t e = cudaGetLastError();
   const int nl = int(net->layers.size());
   // the head is fused into the last decoder convolution, the pooling into

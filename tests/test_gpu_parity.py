@@ -248,3 +248,27 @@ def test_same_result_any_stream_and_repeat(sil):
     s.synchronize()
     torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(ca, cb)
+
+
+@pytest.mark.parametrize("case", ["u8", "u16_nodata", "chip100", "chip300", "filter_off", "narrow_h"])
+def test_vprime_matches_oracle(sil, case):
+    """sil_label_v: the filter's corrected value V' of every pixel, bit-exact,
+    and the same labels and counts as sil_label."""
+    p = {}
+    dtype = np.uint16 if case == "u16_nodata" else np.uint8
+    img, _ = synth.scene(700, 530, 31, n_floes=7, n_haze=2, n_shadow=2, dtype=dtype)
+    if case == "chip100":
+        p = {"chip": 100}
+    elif case == "chip300":
+        p = {"chip": 300}
+    elif case == "filter_off":
+        p = {"filter": 0}
+    elif case == "narrow_h":
+        p = {"lo": [[0, 0, 205], [60, 0, 31], [0, 0, 0]]}
+    dev = torch.from_numpy(img).cuda()
+    lab, vp, cnt = sil.label_v(dev, p)
+    lab1, cnt1, _ = sil.label(dev, p)
+    torch.cuda.synchronize()
+    ovp = oracle.filtered_value(img, p)
+    assert int((vp.cpu().numpy() != ovp).sum()) == 0
+    assert torch.equal(lab, lab1) and torch.equal(cnt, cnt1)

@@ -23,6 +23,7 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
+import oracle  # noqa: E402
 import oracle.unet as U  # noqa: E402
 import synth  # noqa: E402
 
@@ -157,3 +158,33 @@ def test_unet_bounded_wait_runs_out_and_recovers(sil):
     torch.cuda.synchronize()
     assert net.error_count() == errors   # no new errors
     assert np.array_equal(lg.cpu().numpy(), lg0) and np.array_equal(lab.cpu().numpy(), lab0)
+
+
+def test_unet_on_filtered_chips(sil):
+    """The paper's inferencing workflow: the scene is labelled with the
+    filter's V' kept (sil_label_v), chips are cut with their V', and the
+    U-Net runs on the filtered chips.  V' bit-exact against the oracle on the
+    same chips, the filtered input exact, the scores within the bf16 bound."""
+    img, _ = synth.scene(768, 512, 41, n_floes=10, n_haze=3, n_shadow=2)
+    dev = torch.from_numpy(img).cuda()
+    _, vp, _ = sil.label_v(dev, None, labels=False)
+    torch.cuda.synchronize()
+    vp = vp.cpu().numpy()
+    pos = [(0, 0), (1, 1), (2, 0)]
+    chips = np.stack([img[256 * y:256 * y + 256, 256 * x:256 * x + 256] for y, x in pos])
+    vps = np.stack([vp[256 * y:256 * y + 256, 256 * x:256 * x + 256] for y, x in pos])
+    # V' of a chip depends on that chip alone: the oracle on each chip
+    ovps = np.stack([oracle.filtered_value(np.ascontiguousarray(c)) for c in chips])
+    assert np.array_equal(vps, ovps)
+    F, depth = 16, 2
+    wts = synth.unet_weights(F, depth, seed=5)
+    net = sil.UNet(sil.unet_config(F, depth, len(chips)), list(wts.values()))
+    lg = torch.empty(chips.shape[:3] + (3,), dtype=torch.float32, device="cuda")
+    net.forward(torch.from_numpy(chips).cuda(), None, lg, vprime=torch.from_numpy(vps).cuda())
+    torch.cuda.synchronize()
+    x0 = net.tensor(-1).float().cpu().numpy()
+    assert np.array_equal(x0[..., :3], U.prep_filtered(chips, ovps)) and not x0[..., 3:].any()
+    ref, _ = U.forward(chips, wts, depth=depth, vprime_u8=ovps)
+    got = lg.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-2
+    assert net.error_count() == 0
