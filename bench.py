@@ -626,9 +626,10 @@ def run_unet(args):
     img, _ = synth.full_scene(1, SIDE)
     chips_h = synth.chips_from_scene(img, B, seed=3)
     # the filter's V' of the scene (on the GPU), cut at the same chip positions
-    _, vp_dev, _ = sil.label_v(torch.from_numpy(img).cuda(), None, labels=False)
+    scene_dev = torch.from_numpy(img).cuda()
+    _, vp_dev, _ = sil.label_v(scene_dev, None, labels=False)
     vp_h = synth.chips_from_scene(vp_dev.cpu().numpy()[..., None], B, seed=3)[..., 0].copy()
-    del img, vp_dev
+    del img
     wts = synth.unet_weights(F, D, seed=0)
     net = sil.UNet(sil.unet_config(F, D, B), list(wts.values()))
     chips = torch.from_numpy(chips_h).cuda()
@@ -671,6 +672,12 @@ def run_unet(args):
         hl.copy_(lab, non_blocking=True)
     torch.cuda.synchronize()
     te = (time.perf_counter() - te0) / e2e_steps
+    # the whole scene through the workflow: its 1849 chips filtered, batched,
+    # labels written back into the scene's map
+    scene_lab = torch.empty((SIDE, SIDE), dtype=torch.uint8, device="cuda")
+    net.label_scene(scene_dev, vprime=vp_dev, labels=scene_lab)
+    t_scene = _time_cuda(lambda: net.label_scene(scene_dev, vprime=vp_dev, labels=scene_lab), 3, st)
+    del scene_dev, vp_dev, scene_lab
     errors = net.error_count()
     line = {
         "metric": "U-Net chips/s (F=%d, depth %d, bf16 tensor cores)" % (F, D),
@@ -691,6 +698,9 @@ def run_unet(args):
                      "frac_of_burst": achieved / burst, "flops_per_step": flops},
         "clocks": clk.summary(),
         "wait_errors": errors,
+        "scene": {"workload": f"one {SIDE}x{SIDE} scene: {(-(-SIDE // 256)) ** 2} filtered chips through "
+                              f"sil_unet_label_scene", "ms": t_scene * 1e3,
+                  "gpx_per_s": SIDE * SIDE / t_scene / 1e9},
     }
     if not args.no_cpu_baseline:
         import oracle.unet as U

@@ -106,6 +106,18 @@ sil_status sil_unet_forward_filtered(sil_unet* net, const uint8_t* chips, const 
                                      int32_t n, uint8_t* labels, float* logits,
                                      sil_stream stream);
 
+/* The paper's inferencing workflow on a whole scene (Sec. III-C): the
+ * scene (DEVICE uint8 H x W x 3, pitch bytes per row) is cut into its
+ * 256 x 256 chip grid anchored at (0, 0) (zero past the right and bottom
+ * edges), the chips -- filtered by vprime (DEVICE uint8 H x W, the V' of
+ * sil_label_v; NULL: unfiltered) -- run through the network max_batch at a
+ * time, and each chip's labels are written back into labels (DEVICE uint8
+ * H x W, label_pitch bytes per row).  Uses the network's own staging
+ * buffers; asynchronous on `stream`. */
+sil_status sil_unet_label_scene(sil_unet* net, const uint8_t* img, int64_t H, int64_t W,
+                                int64_t pitch, const uint8_t* vprime, int64_t vprime_pitch,
+                                uint8_t* labels, int64_t label_pitch, sil_stream stream);
+
 /* Synchronises the device and returns the number of kernel waits that ran
  * out since the network was created (0 in normal operation). */
 sil_status sil_unet_error_count(sil_unet* net, uint32_t* count);

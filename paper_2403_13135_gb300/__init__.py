@@ -115,6 +115,7 @@ _SIGS = {
     "sil_unet_destroy": ([_P], None),
     "sil_unet_forward": ([_P, _P, _I32, _P, _P, _P], _I32),
     "sil_unet_forward_filtered": ([_P, _P, _P, _I32, _P, _P, _P], _I32),
+    "sil_unet_label_scene": ([_P, _P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P], _I32),
     "sil_unet_error_count": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I32),
     "sil_unet_set_fault": ([_P, _I32], _I32),
     "sil_unet_tensor_shape": ([_P, _I32, ctypes.POINTER(_I64)], _I32),
@@ -480,6 +481,21 @@ class UNet:
     def set_fault(self, layer: int) -> None:
         """Test hook: make layer `layer`'s bounded wait run out (-1 clears)."""
         check(_lib.sil_unet_set_fault(self.handle, int(layer)))
+
+    def label_scene(self, img, vprime=None, labels=None, stream=None):
+        """U-Net labels of a whole device scene (H x W x 3 uint8), chip by chip,
+        on the filtered chips when vprime (H x W uint8, from label_v) is given."""
+        import torch
+        H, W, pitch, dt = _img_geometry(img)
+        if dt != SIL_U8:
+            raise ValueError("label_scene takes uint8 RGB scenes")
+        if labels is None:
+            labels = torch.empty((H, W), dtype=torch.uint8, device=img.device)
+        check(_lib.sil_unet_label_scene(self.handle, img.data_ptr(), H, W, pitch,
+                                        vprime.data_ptr() if vprime is not None else None,
+                                        vprime.stride(0) if vprime is not None else W,
+                                        labels.data_ptr(), labels.stride(0), _stream_handle(stream)))
+        return labels
 
     def error_count(self) -> int:
         v = ctypes.c_uint32()

@@ -542,6 +542,36 @@ __global__ void k_prep_filtered(const uint8_t* __restrict__ chips, const uint8_t
                                               *reinterpret_cast<const uint32_t*>(&b0), 0u, 0u);
 }
 
+// Chips k0 .. k0 + n - 1 of a scene's 256 x 256 grid (gx chips per row) into
+// dense [n][256][256][3] chips and [n][256][256] V' (zero past the scene's
+// edges); one thread per chip pixel.
+__global__ void k_gather_chips(const uint8_t* __restrict__ img, int64_t H, int64_t W, int64_t pitch,
+                               const uint8_t* __restrict__ vp, int64_t vpitch, int64_t k0, int gx,
+                               int64_t P, uint8_t* __restrict__ chips, uint8_t* __restrict__ vout) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  const int64_t k = k0 + t / (kChip * kChip);
+  const int rem = int(t % (kChip * kChip)), y = rem / kChip, x = rem % kChip;
+  const int64_t sy = (k / gx) * kChip + y, sx = (k % gx) * kChip + x;
+  const bool in = sy < H && sx < W;
+  const uint8_t* s = img + sy * pitch + 3 * sx;
+  chips[3 * t] = in ? s[0] : 0;
+  chips[3 * t + 1] = in ? s[1] : 0;
+  chips[3 * t + 2] = in ? s[2] : 0;
+  if (vout) vout[t] = in ? vp[sy * vpitch + sx] : 0;
+}
+
+// Chip labels back into the scene's label map (the part inside the scene).
+__global__ void k_scatter_labels(const uint8_t* __restrict__ lab, int64_t k0, int gx, int64_t P,
+                                 int64_t H, int64_t W, uint8_t* __restrict__ out, int64_t opitch) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  const int64_t k = k0 + t / (kChip * kChip);
+  const int rem = int(t % (kChip * kChip)), y = rem / kChip, x = rem % kChip;
+  const int64_t sy = (k / gx) * kChip + y, sx = (k % gx) * kChip + x;
+  if (sy < H && sx < W) out[sy * opitch + sx] = lab[t];
+}
+
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
@@ -579,6 +609,10 @@ struct sil_unet {
   unsigned int* err = nullptr;
   int last_n = 0;
   int fault_layer = -1;  // test hook (sil_unet_set_fault)
+  // staging of sil_unet_label_scene: max_batch chips, their V' and labels
+  uint8_t* stage_chips = nullptr;
+  uint8_t* stage_vp = nullptr;
+  uint8_t* stage_lab = nullptr;
 };
 
 namespace {
@@ -888,6 +922,9 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
   }
   const Tensor b0 = act(kChip >> D, width(D)), b1 = act(kChip >> D, width(D));
   net->err = static_cast<unsigned int*>(dalloc(sizeof(unsigned int)));
+  net->stage_chips = static_cast<uint8_t*>(dalloc(size_t(B) * kChip * kChip * 3));
+  net->stage_vp = static_cast<uint8_t*>(dalloc(size_t(B) * kChip * kChip));
+  net->stage_lab = static_cast<uint8_t*>(dalloc(size_t(B) * kChip * kChip));
   if (st == SIL_OK && cudaMemset(net->err, 0, sizeof(unsigned int)) != cudaSuccess) st = SIL_ECUDA;
   auto skip_of = [&](int l) {  // encoder output of level l: second half of cat[l]
     Tensor s = cat[l];
@@ -1046,6 +1083,42 @@ extern "C" sil_status sil_unet_set_fault(sil_unet* net, int32_t layer) {
     return SIL_EINVAL;
   }
   net->fault_layer = layer;
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_label_scene(sil_unet* net, const uint8_t* img, int64_t H,
+                                           int64_t W, int64_t pitch, const uint8_t* vprime,
+                                           int64_t vprime_pitch, uint8_t* labels,
+                                           int64_t label_pitch, sil_stream stream) {
+  if (!net || !img || !labels || H < 1 || W < 1 || pitch < 3 * W || label_pitch < W ||
+      (vprime && vprime_pitch < W)) {
+    set_error("sil_unet_label_scene: NULL pointer or bad geometry");
+    return SIL_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int gx = int((W + kChip - 1) / kChip), gy = int((H + kChip - 1) / kChip);
+  const int64_t nchips = int64_t(gx) * gy;
+  for (int64_t k0 = 0; k0 < nchips; k0 += net->cfg.max_batch) {
+    const int n = int(nchips - k0 < net->cfg.max_batch ? nchips - k0 : net->cfg.max_batch);
+    const int64_t P = int64_t(n) * kChip * kChip;
+    const unsigned blocks = unsigned((P + 255) / 256);
+    k_gather_chips<<<blocks, 256, 0, s>>>(img, H, W, pitch, vprime, vprime_pitch, k0, gx, P,
+                                          net->stage_chips, vprime ? net->stage_vp : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error("sil_unet_label_scene: gather: %s", cudaGetErrorString(e));
+      return SIL_ECUDA;
+    }
+    const sil_status st = sil_unet_forward_filtered(net, net->stage_chips, vprime ? net->stage_vp : nullptr,
+                                                    n, net->stage_lab, nullptr, stream);
+    if (st != SIL_OK) return st;
+    k_scatter_labels<<<blocks, 256, 0, s>>>(net->stage_lab, k0, gx, P, H, W, labels, label_pitch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error("sil_unet_label_scene: scatter: %s", cudaGetErrorString(e));
+      return SIL_ECUDA;
+    }
+  }
   return SIL_OK;
 }
 

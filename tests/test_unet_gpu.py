@@ -188,3 +188,38 @@ def test_unet_on_filtered_chips(sil):
     got = lg.cpu().numpy()
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-2
     assert net.error_count() == 0
+
+
+def test_unet_label_scene_matches_chips(sil):
+    """sil_unet_label_scene: the scene's chip grid (zero past the edges) with
+    its V', max_batch chips at a time, labels written back -- equal, bit for
+    bit, to cutting the same chips by hand and running them one batch each."""
+    img, _ = synth.scene(700, 530, 43, n_floes=9, n_haze=2, n_shadow=2)
+    H, W, _ = img.shape
+    dev = torch.from_numpy(img).cuda()
+    _, vp, _ = sil.label_v(dev, None, labels=False)
+    F, depth = 16, 2
+    wts = synth.unet_weights(F, depth, seed=6)
+    net = sil.UNet(sil.unet_config(F, depth, 4), list(wts.values()))   # 9 chips: batches 4, 4, 1
+    lab = net.label_scene(dev, vprime=vp)
+    torch.cuda.synchronize()
+    assert net.error_count() == 0
+    vp_h = vp.cpu().numpy()
+    gy, gx = -(-H // 256), -(-W // 256)
+    chips = np.zeros((gy * gx, 256, 256, 3), np.uint8)
+    vps = np.zeros((gy * gx, 256, 256), np.uint8)
+    for k in range(gy * gx):
+        cy, cx = divmod(k, gx)
+        part = img[cy * 256:cy * 256 + 256, cx * 256:cx * 256 + 256]
+        chips[k, :part.shape[0], :part.shape[1]] = part
+        vps[k, :part.shape[0], :part.shape[1]] = vp_h[cy * 256:cy * 256 + 256, cx * 256:cx * 256 + 256]
+    want = np.zeros((gy * 256, gx * 256), np.uint8)
+    for k0 in range(0, gy * gx, 4):
+        c = torch.from_numpy(chips[k0:k0 + 4]).cuda()
+        lb = torch.empty(c.shape[:3], dtype=torch.uint8, device="cuda")
+        net.forward(c, lb, vprime=torch.from_numpy(vps[k0:k0 + 4]).cuda())
+        torch.cuda.synchronize()
+        for i, l in enumerate(lb.cpu().numpy()):
+            cy, cx = divmod(k0 + i, gx)
+            want[cy * 256:cy * 256 + 256, cx * 256:cx * 256 + 256] = l
+    assert np.array_equal(lab.cpu().numpy(), want[:H, :W])
