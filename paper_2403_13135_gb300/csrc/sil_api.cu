@@ -463,11 +463,30 @@ sil_status sil_label_host(const void* img, int64_t H, int64_t W, int64_t pitch_b
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   uint8_t* dimg = static_cast<uint8_t*>(g.img);
   const uint8_t* himg = static_cast<const uint8_t*>(img);
-  // about SIL_HOST_STRIPES stripes of whole chip rows
-  int64_t ks = gy / SIL_HOST_STRIPES;
-  if (ks < 1) ks = 1;
-  if ((gy + ks - 1) / ks > kMaxStripes) ks = (gy + kMaxStripes - 1) / kMaxStripes;
-  const int nstripes = int((gy + ks - 1) / ks);
+  // stripes of whole chip rows: one chip row first and last (the copy in of
+  // the first and the labelling and copy out of the last are not overlapped
+  // with anything), about SIL_HOST_STRIPES - 2 equal ones between
+  int64_t cut[kMaxStripes + 1];
+  int nstripes = 0;
+  {
+    const int64_t mid = gy > 2 ? gy - 2 : 0;
+    int64_t ks = mid / (SIL_HOST_STRIPES - 2);
+    if (ks < 1) ks = 1;
+    if ((mid + ks - 1) / ks > kMaxStripes - 2) ks = (mid + kMaxStripes - 3) / (kMaxStripes - 2);
+    int64_t row = 0;
+    cut[0] = 0;
+    auto add = [&](int64_t rows) {
+      row = row + rows < gy ? row + rows : gy;
+      cut[++nstripes] = row;
+    };
+    if (gy > 2) {
+      add(1);
+      while (row < gy - 1) add(row + ks < gy - 1 ? ks : gy - 1 - row);
+      add(1);
+    } else {
+      while (row < gy) add(1);
+    }
+  }
   Req r;
   r.W = W;
   r.pitch = pitch_bytes;
@@ -481,8 +500,8 @@ sil_status sil_label_host(const void* img, int64_t H, int64_t W, int64_t pitch_b
   if (e == cudaSuccess) e = cudaStreamWaitEvent(g.out, g.start, 0);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.cnt, 0, 32, s);
   for (int i = 0; i < nstripes && e == cudaSuccess; ++i) {
-    const int64_t r0 = int64_t(i) * ks * chip;
-    const int64_t r1 = r0 + ks * chip < H ? r0 + ks * chip : H;
+    const int64_t r0 = cut[i] * chip;
+    const int64_t r1 = cut[i + 1] * chip < H ? cut[i + 1] * chip : H;
     const int64_t rows = r1 - r0;
     // copy in (the last row only up to its last pixel)
     if (pitch_bytes == row_bytes)
