@@ -143,7 +143,12 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
 
 template <int NT>
 struct ConvCfg {
-  static constexpr int kStages = NT >= 128 ? 3 : 4;
+  // Narrow tiles (NT <= 32) run three CTAs per SM with three stages each:
+  // their per-stage time is set by the single producer and MMA threads'
+  // instruction latencies (a stage is only 64 tensor-pipe cycles of work),
+  // so more independent CTAs per SM beat a deeper ring; wider tiles run two.
+  static constexpr int kMinBlocks = NT <= 32 ? 3 : 2;
+  static constexpr int kStages = NT >= 128 ? 3 : (NT <= 32 ? 3 : 4);
   static constexpr int kA = kBM * kBK * 2;
   static constexpr int kB = NT * kBK * 2;
   static constexpr int kStage = kA + kB;
@@ -161,7 +166,7 @@ struct ConvCfg {
 // t / ntiles, N tile t % ntiles).  Warps 0-3 produce A/B stages, warps 4-7
 // drain the accumulators, warp 8 issues the MMAs.
 template <int NT>
-__global__ void __launch_bounds__(kConvThreads, 2)
+__global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
     k_conv(const ConvArgs a, const __grid_constant__ CUtensorMap tmap, int ntiles, int ntotal) {
   using C = ConvCfg<NT>;
   constexpr int S = C::kStages;

@@ -272,3 +272,46 @@ def test_vprime_matches_oracle(sil, case):
     ovp = oracle.filtered_value(img, p)
     assert int((vp.cpu().numpy() != ovp).sum()) == 0
     assert torch.equal(lab, lab1) and torch.equal(cnt, cnt1)
+
+
+def test_image_beyond_4gib(sil):
+    """A 38000 x 38000 u8 image (4.33 GB in, 1.44 GB of labels): byte offsets
+    past 2^32 in every address of the last chip rows.  The image tiles a
+    2000 x 2000 scene (a period that is not a multiple of the chip, so the
+    chips differ) with a different scene in its bottom-right corner; sampled
+    chips there and elsewhere against the oracle on chip-aligned crops, the
+    totals against the sum of the chip counts, and the host entry point equal
+    to the device one."""
+    base, _ = synth.scene(2000, 2000, 5, n_floes=30, n_haze=2, n_shadow=2)
+    img = np.tile(base, (19, 19, 1))
+    H, W, _ = img.shape
+    corner, _ = synth.scene(600, 900, 7, n_floes=6, n_haze=1, n_shadow=1)
+    img[H - 600:, W - 900:] = corner
+    assert (H - 1) * W * 3 > 2 ** 32
+    dev = torch.from_numpy(img).cuda()
+    lab, cnt, cc = sil.label(dev, None, chip_counts=True)
+    torch.cuda.synchronize()
+    del dev
+    cnt = cnt.cpu().numpy()
+    cc = cc.cpu().numpy().astype(np.int64)
+    lab_h = lab.cpu().numpy()
+    del lab
+    assert int(cnt.sum()) == H * W
+    np.testing.assert_array_equal(cc.sum(axis=(0, 1)), cnt)
+    gy, gx = cc.shape[:2]
+    assert (gy, gx) == (149, 149)
+    picks = {(0, 0), (0, gx - 1), (gy - 1, 0), (gy - 1, gx - 1), (gy - 2, gx - 3),
+             (gy - 3, gx - 2), (gy - 1, gx - 4), (gy // 2, gx // 2)}
+    rng = np.random.default_rng(8)
+    while len(picks) < 16:
+        picks.add((int(rng.integers(0, gy)), int(rng.integers(0, gx))))
+    for (cy, cx) in sorted(picks):
+        y0, x0 = cy * 256, cx * 256
+        crop = np.ascontiguousarray(img[y0:y0 + 256, x0:x0 + 256])
+        olab, _, occ, _ = oracle.label(crop)
+        np.testing.assert_array_equal(cc[cy, cx], occ[0, 0].astype(np.int64))
+        assert int((lab_h[y0:y0 + 256, x0:x0 + 256] != olab).sum()) == 0, (cy, cx)
+    hlab, hcnt, hcc = sil.label_host(img, None, chip_counts=True)
+    assert np.array_equal(hlab, lab_h)
+    np.testing.assert_array_equal(hcnt.astype(np.uint64), cnt.astype(np.uint64))
+    np.testing.assert_array_equal(hcc.astype(np.int64), cc)
