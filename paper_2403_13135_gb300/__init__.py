@@ -215,9 +215,10 @@ def label(img, p=None, *, labels=True, chip_counts=False, out_labels=None,
     return lab, cnt, cc
 
 
-def label_v(img, p=None, *, labels=True, stream=None):
+def label_v(img, p=None, *, labels=True, chip_counts=False, stream=None):
     """Like ``label`` plus the filter's corrected value V' of every pixel
-    (uint8 H x W; sil_label_v).  Returns (labels or None, vprime, counts)."""
+    (uint8 H x W; sil_label_v).  Returns (labels or None, vprime, counts),
+    and the chip counts as a fourth item when ``chip_counts``."""
     import torch
     H, W, pitch, dt = _img_geometry(img)
     pp = _as_params(p)
@@ -225,10 +226,14 @@ def label_v(img, p=None, *, labels=True, stream=None):
     lab = torch.empty((H, W), dtype=torch.uint8, device=dev) if labels else None
     vp = torch.empty((H, W), dtype=torch.uint8, device=dev)
     cnt = torch.empty(4, dtype=torch.int64, device=dev)
+    cc = None
+    if chip_counts:
+        cc = torch.empty((-(-H // pp.chip), -(-W // pp.chip), 4), dtype=torch.int32, device=dev)
     check(_lib.sil_label_v(img.data_ptr(), H, W, pitch, dt, ctypes.byref(pp),
                            lab.data_ptr() if lab is not None else None, W, vp.data_ptr(), W,
-                           cnt.data_ptr(), None, _stream_handle(stream)))
-    return lab, vp, cnt
+                           cnt.data_ptr(), cc.data_ptr() if cc is not None else None,
+                           _stream_handle(stream)))
+    return (lab, vp, cnt, cc) if chip_counts else (lab, vp, cnt)
 
 
 def label_host(img: np.ndarray, p=None, *, labels=True, chip_counts=False, stream=None):

@@ -30,6 +30,7 @@
 // need a shuffle.  The median of three is a+b+c-max3-min3, exact in 32-bit
 // wrap-around arithmetic because every lane of the result lies in [0,65535].
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -47,9 +48,10 @@ constexpr int kPlaneStride = 256;
 constexpr int kRing = SIL_RING;  // row slots per band
 constexpr int kLanePx = 16;
 
-// Per-chip statistics scratch (shared memory).
+// Per-chip statistics scratch (shared memory).  hist[256 + lane] are bins
+// that nothing reads: lanes past a narrow chip's last column count there.
 struct ChipStat {
-  uint32_t hist[256];
+  uint32_t hist[256 + 32];
   uint32_t red[kWarps][4];
   uint32_t nod[kWarps];
   int32_t stat[8];
@@ -376,11 +378,21 @@ __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const
   // Histogram of Vf over valid, non-nodata pixels; the bin index is byte 1
   // (low lane) or byte 3 (high lane) of each word.
   uint32_t* hist = sm.st.hist;
-  if (!kFlags && (FULL || nvalid == 16)) {
+  if (!kFlags && FULL) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       atomicAdd(&hist[__byte_perm(out[i], 0, 0x4441)], 1u);
       atomicAdd(&hist[__byte_perm(out[i], 0, 0x4443)], 1u);
+    }
+  } else if (!kFlags) {
+    // a chip narrower than 256: the same adds in every lane (no branch that
+    // would split each half-warp), pixels past the chip's last column
+    // counted into the lane's own unread bin
+    const uint32_t unread = 256u + (threadIdx.x & 31u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      atomicAdd(&hist[i < nvalid ? __byte_perm(out[i], 0, 0x4441) : unread], 1u);
+      atomicAdd(&hist[i + 8 < nvalid ? __byte_perm(out[i], 0, 0x4443) : unread], 1u);
     }
   } else {
 #pragma unroll
@@ -858,17 +870,33 @@ __device__ __forceinline__ void band_vprime(uint8_t* out, int64_t pitch, int64_t
 
 // ---------------------------------------------------------------------------
 // The whole chip.  All threads of the CTA must call it.
+// kSplit > 1: the CTA is rank q of a cluster of kSplit CTAs that label the
+// chip together; it filters rows [q h / kSplit, (q + 1) h / kSplit) (the
+// median's neighbours outside that slice are read from the image like any
+// other row, clamped to the chip), the slices' histograms are summed through
+// distributed shared memory, every CTA derives the same statistics and
+// table from the sum, labels its own rows, and rank 0 alone writes the
+// chip's counts.  (8-bit images without H/S ranges only: those keep no
+// per-pixel flags.)
 // ---------------------------------------------------------------------------
-template <int DT, bool HS, class SM>
+template <int DT, bool HS, int kSplit = 1, class SM>
 __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, int chip,
                                            int64_t cy, int64_t cx, SM& sm, uint8_t* lut,
                                            uint8_t* vlut) {
+  static_assert(kSplit == 1 || (DT == SIL_U8 && !HS), "split chips: 8-bit, no H/S ranges");
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, band = tid >> 4;
   const int64_t y0 = cy * chip, x0 = cx * chip;
   const int h = int(min(int64_t(chip), r.H - y0));
   const int w = int(min(int64_t(chip), r.W - x0));
+  int s0 = 0, s1 = h;
+  unsigned rank = 0;
+  if (kSplit > 1) {
+    rank = cooperative_groups::this_cluster().block_rank();
+    s0 = int(rank) * h / kSplit;
+    s1 = (int(rank) + 1) * h / kSplit;
+  }
   // balanced row bands, one per half-warp
-  const int r0 = (band * h) / kBands, r1 = ((band + 1) * h) / kBands;
+  const int r0 = s0 + (band * (s1 - s0)) / kBands, r1 = s0 + ((band + 1) * (s1 - s0)) / kBands;
 
   __syncthreads();  // the previous chip of a persistent CTA is done with sm
   if (tid < 256) sm.st.hist[tid] = 0;
@@ -895,6 +923,19 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
     if (lane == 0) sm.st.nod[wid] = n_nodata;
   }
   __syncthreads();
+  if (kSplit > 1) {
+    // the chip's histogram = the sum of the slices' histograms
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    cl.sync();  // every slice's histogram is complete
+    uint32_t v = 0;
+    if (tid < 256) {
+#pragma unroll
+      for (int q = 0; q < kSplit; ++q) v += cl.map_shared_rank(sm.st.hist, q)[tid];
+    }
+    cl.sync();  // every CTA has read every histogram
+    if (tid < 256) sm.st.hist[tid] = v;
+    __syncthreads();
+  }
   {
     uint32_t nd = 0;
     if (DT == SIL_U16) {
@@ -959,8 +1000,10 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
     for (int k = 0; k < nw; ++k) v += sm.st.red[k][c];
     // nodata pixels are left out of the histogram and always masked
     if (!HS && c == 3) v += uint32_t(h * w) - uint32_t(sm.st.stat[kStatN]);
-    if (r.chip_counts) r.chip_counts[(cy * r.gx + cx) * 4 + c] = v;
-    atomicAdd(&r.counts[c], (unsigned long long)v);
+    if (rank == 0) {
+      if (r.chip_counts) r.chip_counts[(cy * r.gx + cx) * 4 + c] = v;
+      atomicAdd(&r.counts[c], (unsigned long long)v);
+    }
   }
 }
 

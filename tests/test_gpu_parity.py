@@ -315,3 +315,35 @@ def test_image_beyond_4gib(sil):
     assert np.array_equal(hlab, lab_h)
     np.testing.assert_array_equal(hcnt.astype(np.uint64), cnt.astype(np.uint64))
     np.testing.assert_array_equal(hcc.astype(np.int64), cc)
+
+
+@pytest.mark.parametrize("case", ["chip256", "chip256_counts_only", "chip100", "chip8", "one_wave_limit"])
+def test_split_chips_match_oracle(sil, case):
+    """Requests with few chips (four CTAs per chip fit in one wave of
+    resident CTAs) are labelled by clusters of four CTAs, one row slice each,
+    with the histogram summed across the cluster; "one_wave_limit" has the
+    largest such chip count on this GPU, plus one (whole-chip path).  Whole
+    images against the oracle: labels, V', counts and chip counts
+    bit-exact."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    p = {}
+    if case.startswith("chip256"):
+        H, W = 1000, 1500                          # 4 x 6 chips, ragged edges
+    elif case == "chip100":
+        H, W, p = 700, 530, {"chip": 100}
+    elif case == "chip8":
+        H, W, p = 64, 61, {"chip": 8}
+    else:
+        n = (2 * sms) // 4 + 1                     # two CTAs per SM on this GPU
+        H, W, p = 64, 64 * n - 5, {"chip": 64}
+    img, _ = synth.scene(H, W, 47, n_floes=9, n_haze=2, n_shadow=2)
+    dev = torch.from_numpy(img).cuda()
+    want_labels = case != "chip256_counts_only"
+    lab, vp, cnt, cc = sil.label_v(dev, p, labels=want_labels, chip_counts=True)
+    torch.cuda.synchronize()
+    olab, ocnt, occ, _ = oracle.label(img, p)
+    if want_labels:
+        assert int((lab.cpu().numpy() != olab).sum()) == 0
+    np.testing.assert_array_equal(vp.cpu().numpy(), oracle.filtered_value(img, p))
+    np.testing.assert_array_equal(cnt.cpu().numpy().astype(np.uint64), ocnt)
+    np.testing.assert_array_equal(cc.cpu().numpy().astype(np.uint32), occ)
