@@ -62,6 +62,7 @@ struct alignas(16) StatScratch {
   uint64_t bnum_lo[kWarps];
   uint32_t bnum_hi[kWarps], bden[kWarps];
   int32_t bt[kWarps], lo[kWarps], hi[kWarps];
+  float fmax[kWarps];
   uint32_t n0;
 };
 
@@ -647,9 +648,14 @@ __device__ __forceinline__ void chip_stats_block(ChipStat& st, StatScratch& sc,
   }
   c += pc;  // pixels with Vf <= tid
   s += ps;
+  if (hi < 0) {  // no pixel: the statistics of an empty chip
+    lo = 0;
+    hi = 0;
+  }
   int t = -1;
   uint64_t nlo = 0;
   uint32_t nhi = 0, den = 0;
+  float f = -1.f;
   if (tid <= 254 && c > 0 && c < N) {
     const uint64_t D = uint64_t(ST) * c - uint64_t(N) * s;  // >= 0
     const unsigned __int128 num = (unsigned __int128)D * D;
@@ -657,7 +663,42 @@ __device__ __forceinline__ void chip_stats_block(ChipStat& st, StatScratch& sc,
     nhi = uint32_t(num >> 64);
     den = c * (N - c);
     t = tid;
+    const float fd = float(D);
+    f = fd * fd / float(den);
   }
+  // Float pre-filter: each float score is within 3e-7 (relative) of the
+  // exact one (three roundings and two conversions of 2^-24 each), so every
+  // threshold whose exact score is the largest has a float score within
+  // 4e-6 of the largest float score.  Only those candidates are compared
+  // exactly; when there is one, it is the answer.
+  float m = f;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if (lane == 0) sc.fmax[wid] = m;
+  __syncthreads();
+  float M = -1.f;
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) M = fmaxf(M, sc.fmax[k]);
+  const bool cand = t >= 0 && f >= M * (1.0f - 4e-6f);
+  const int ncand = __syncthreads_count(cand);
+  if (ncand <= 1) {
+    // one candidate, or none (no split: t = lo); that thread's inclusive
+    // prefix count is n0
+    if (ncand == 1 ? cand : tid == lo) {
+      const uint32_t n0 = c, n1 = N - n0;
+      st.stat[kStatLo] = lo;
+      st.stat[kStatHi] = hi;
+      st.stat[kStatT] = tid;
+      st.stat[kStatN] = int(N);
+      st.stat[kStatN0] = int(n0);
+      st.stat[kStatGate] = (hi - lo >= dp.mm_min_range) && (uint64_t(dp.frac_den) * n0 >= N) &&
+                           (uint64_t(dp.frac_den) * n1 >= N) && N > 0;
+    }
+    __syncthreads();
+    return;
+  }
+  // several candidates (ties or near-ties): exact argmax among them
+  if (!cand) t = -1;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const uint64_t o_lo = __shfl_xor_sync(0xffffffffu, nlo, off);
