@@ -35,7 +35,7 @@ CHIP = 256
 # DRAM bytes (read + write) of one labeler launch on this workload, from the
 # ncu capture summarised in profiles/k_label_u8_scene10980.md; reset to None
 # whenever the kernel changes, until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = (364.537856 + 92.945664) * 1e6
+TRAFFIC_BYTES_PER_LAUNCH = (364.527104 + 92.852992) * 1e6
 METRIC = "Gpixel/s labeled (bit-exact)"
 UNIT = "Gpixel/s"
 
