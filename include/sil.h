@@ -123,7 +123,10 @@ int sil_version(void);
  *                entry per chip of the grid anchored at (0,0); may be NULL.
  * Statistics (Otsu, min/max) are taken per chip (Sec. III-A / III-C: the
  * paper filters 256 x 256 chips).  Nothing is allocated; the call only
- * enqueues a memset of counts and one kernel. */
+ * enqueues a memset of counts and one kernel.  (uint8 requests without H/S
+ * ranges whose chips number at most a quarter of the device's resident
+ * CTAs run on clusters of four CTAs per chip, one row slice each; the
+ * results are the same bit for bit.) */
 sil_status sil_label(const void* img, int64_t H, int64_t W, int64_t pitch_bytes,
                      sil_dtype dt, const sil_params* p, uint8_t* labels,
                      int64_t label_pitch, uint64_t* counts,
