@@ -32,9 +32,9 @@ if ROOT not in sys.path:
 
 SIDE = 10980
 CHIP = 256
-# DRAM bytes (read + write) of one labeler launch on this workload, from the
-# ncu capture summarised in profiles/k_label_u8_scene10980.md; reset to None
-# whenever the kernel changes, until it is captured again.
+# DRAM bytes (read + write) of one labeler launch on this workload, from an
+# ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); None whenever the kernel has changed since.
 TRAFFIC_BYTES_PER_LAUNCH = (364.527104 + 92.852992) * 1e6
 METRIC = "Gpixel/s labeled (bit-exact)"
 UNIT = "Gpixel/s"
@@ -62,6 +62,7 @@ class ClockSampler:
         self._stop = threading.Event()
         self._th = None
         self._t0 = self._t1 = None
+        self._regions = {}
 
     def _run(self):
         while not self._stop.is_set():
@@ -78,30 +79,26 @@ class ClockSampler:
         self._th = threading.Thread(target=self._run, daemon=True)
         self._th.start()
 
-    def mark(self, t0, t1):
-        self._t0, self._t1 = t0, t1
+    def mark(self, t0, t1, name="timed"):
+        self._regions[name] = (t0, t1)
+        if name == "timed":
+            self._t0, self._t1 = t0, t1
 
     def stop(self):
         self._stop.set()
         if self._th:
             self._th.join(timeout=10)
 
-    def summary(self):
+    def _rows(self):
         rows = []
         for t, line in self.samples:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            rows.append((t, parts))
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
-        inside = [r for r in rows if self._t0 is not None and self._t0 <= r[0] <= self._t1]
-        note = []
-        if not inside:
-            # the region is shorter than one sample: take the samples closest to it
-            mid = 0.5 * (self._t0 + self._t1) if self._t0 is not None else rows[-1][0]
-            inside = sorted(rows, key=lambda r: abs(r[0] - mid))[:2]
-            note.append("timed region shorter than the sampling interval; nearest samples")
+            if len(parts) >= 9:
+                rows.append((t, parts))
+        return rows
+
+    @staticmethod
+    def _stats(inside):
         sm = sorted(float(r[1][1]) for r in inside)
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -109,9 +106,28 @@ class ClockSampler:
             for n, v in zip(names, p[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        pw = [float(r[1][3]) for r in inside if r[1][3] not in ("", "[N/A]")]
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(inside[0][1][2]),
-                "power_w_max": max(float(r[1][3]) for r in inside if r[1][3] not in ("", "[N/A]")),
-                "samples": len(inside), "reasons": sorted(reasons) + note}
+                "power_w_max": max(pw) if pw else None, "samples": len(inside),
+                "reasons": sorted(reasons)}
+
+    def summary(self, name="timed"):
+        """Clock statistics of the samples taken inside the named region
+        (the nearest two, with a note, when the region is shorter than the
+        sampling interval)."""
+        rows = self._rows()
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        t0, t1 = self._regions.get(name, (None, None))
+        inside = [r for r in rows if t0 is not None and t0 <= r[0] <= t1]
+        note = []
+        if not inside:
+            mid = 0.5 * (t0 + t1) if t0 is not None else rows[-1][0]
+            inside = sorted(rows, key=lambda r: abs(r[0] - mid))[:2]
+            note.append("region shorter than the sampling interval; nearest samples")
+        out = self._stats(inside)
+        out["reasons"] = out["reasons"] + note
+        return out
 
 
 def _dist():
@@ -307,6 +323,17 @@ def run_sil(args):
     if ws > 1:
         torch.distributed.barrier()
     sampler.mark(t0, t1)
+    # clock soak: the same step for at least args.soak seconds right after
+    # the timed region, so that the clocks the timed steps ran at are
+    # sampled many times even when the timed region is short
+    ts0 = time.monotonic()
+    n_soak = 0
+    while time.monotonic() - ts0 < args.soak:
+        for _ in range(200):
+            step()
+        n_soak += 200
+        torch.cuda.synchronize()
+    sampler.mark(ts0, time.monotonic(), "soak")
     time.sleep(0.2)
     sampler.stop()
     elapsed = start.elapsed_time(end) / 1e3
@@ -347,6 +374,12 @@ def run_sil(args):
     avg_launch = float(per_launch.mean())
     achieved = alg_bytes / avg_launch / 1e9
     clocks = sampler.summary()
+    soak = sampler.summary("soak")
+    soak["steps"] = n_soak
+    clocks["soak"] = soak
+    if clocks.get("sm_mhz") and soak.get("sm_mhz"):
+        # time x clock: the step's cycle count, comparable across clock states
+        clocks["ms_per_step_x_soak_mhz"] = el_max / args.steps * 1e3 * soak["sm_mhz"]
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -382,20 +415,6 @@ def run_sil(args):
     return 0
 
 
-def _crop_tiles(img, shapes, seed=0):
-    """Tiles of the given shapes cut at seeded positions out of a scene (same
-    generator, no per-tile generation cost)."""
-    rng = np.random.default_rng(seed)
-    H, W, _ = img.shape
-    out = []
-    for (h, w, _s) in shapes:
-        h, w = min(h, H), min(w, W)
-        y = int(rng.integers(0, H - h + 1))
-        x = int(rng.integers(0, W - w + 1))
-        out.append(np.ascontiguousarray(img[y:y + h, x:x + w]))
-    return out
-
-
 def _time_cuda(fn, reps, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -416,7 +435,7 @@ def run_batch(args):
     import synth
     scene, _ = synth.full_scene(1, SIDE)
     shapes = synth.uneven_tile_shapes(args.tiles)
-    tiles = _crop_tiles(scene, shapes)
+    tiles, _ = synth.crop_tiles(scene, shapes, seed=0)
     npx = sum(t.shape[0] * t.shape[1] for t in tiles)
     dev = [torch.from_numpy(t).cuda() for t in tiles]
     labs = [torch.empty(t.shape[:2], dtype=torch.uint8, device="cuda") for t in tiles]
@@ -724,10 +743,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="sil", choices=["sil", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--soak", type=float, default=1.5,
+                    help="seconds of extra steps after the timed region, for clock samples")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--traffic", type=float, default=TRAFFIC_BYTES_PER_LAUNCH,
-                    help="ncu dram bytes per launch of the labeler (from profiles/)")
+                    help="ncu DRAM bytes per launch of the labeler")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0,
                     help="oracle worker processes for the CPU baseline (0 = every host core)")

@@ -202,13 +202,18 @@ sil_status sil_label_batch(const sil_tile* tiles, int32_t n, sil_dtype dt,
  *   tiles  host array of n descriptors, 1 <= n <= 256; more is rejected
  *          with SIL_EINVAL and a message naming the limit.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any
- * stream capture.  Every call shares the array and leaves the last call's
- * descriptors in it (the queue head and each tile's counts are zeroed by
- * the call itself): calls whose work overlaps on the GPU -- for example on
- * two streams without ordering between them -- race and must not be made;
- * calls on one stream are ordered.  Calls no cudaMalloc, cudaFree or other
- * allocating routine.  Asynchronous on `stream`. */
+ * device and CUDA context, with that device current; again after the
+ * context has been replaced, e.g. by cudaDeviceReset).  Every call shares
+ * the array and leaves the last call's descriptors in it (the queue head
+ * and each tile's counts are zeroed by the call itself): calls whose work
+ * overlaps on the GPU -- for example on two streams without ordering
+ * between them -- race and must not be made; calls on one stream are
+ * ordered.  The descriptors are copied to the array from the call's own
+ * stack (pageable memory), so the call may block the host until earlier
+ * work on `stream` has drained, and it returns SIL_EINVAL without doing
+ * anything while `stream` is being captured (a recorded copy would read
+ * that stack after the call returned).  Calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Asynchronous on `stream` otherwise. */
 sil_status sil_label_batch_noalloc(const sil_tile* tiles, int32_t n, sil_dtype dt,
                                    const sil_params* p, sil_stream stream);
 

@@ -36,16 +36,46 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name is not a device address).
+// Identity of the device's current context (cuCtxGetCurrent + cuCtxGetId,
+// fetched through the runtime so the library does not link libcuda): a
+// cudaDeviceReset in this process ends the context and reloads the module,
+// after which the array has a new address.  0 if unavailable.
+unsigned long long current_context_id() {
+  using GetCurrentFn = int (*)(void**);
+  using GetIdFn = int (*)(void*, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(p);
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device (the host-side
+// name is not a device address).  Looked up once per device and context:
+// again after the device's context has been replaced.
 sil_status scratch_address(int dev, unsigned char** out) {
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("sil_label_batch_noalloc: device %d out of range", dev);
     return SIL_EINVAL;
   }
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> g(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -53,6 +83,8 @@ sil_status scratch_address(int dev, unsigned char** out) {
       return SIL_ECUDA;
     }
     g_scratch_addr[dev] = p;
+    // the lookup creates the device's context if there was none yet
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
   return SIL_OK;
@@ -78,6 +110,15 @@ extern "C" sil_status sil_label_batch_noalloc(const sil_tile* tiles, int32_t n, 
   DevParams dp;
   sil_status st = derive_params(p, &dp);
   if (st != SIL_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // The descriptors are copied from this call's stack: a copy recorded into
+  // a graph would read that memory after the call has returned.
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap_st) != cudaSuccess || cap_st != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    set_error("sil_label_batch_noalloc: the stream is being captured; this call cannot be captured");
+    return SIL_EINVAL;
+  }
   const int chip = p ? p->chip : 256;
   // descriptors built on the stack, copied into the device array
   Req reqs[kNoAllocMaxTiles];
@@ -111,9 +152,9 @@ extern "C" sil_status sil_label_batch_noalloc(const sil_tile* tiles, int32_t n, 
   Req* d_reqs = reinterpret_cast<Req*>(base);
   int64_t* d_prefix = reinterpret_cast<int64_t*>(base + kPrefixOff);
   unsigned long long* d_head = reinterpret_cast<unsigned long long*>(base + kHeadOff);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // Pageable-source copies return once the source bytes are staged, so the
-  // stack arrays may go out of scope afterwards.
+  // Copies from pageable memory return once the source bytes are staged
+  // (which can block the host until earlier work on the stream is done), so
+  // the stack arrays may go out of scope afterwards.
   cudaError_t e = cudaMemcpyAsync(d_reqs, reqs, sizeof(Req) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_prefix, prefix, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);

@@ -220,3 +220,31 @@ def chips_from_scene(img: np.ndarray, n: int, seed: int = 0, chip: int = 256) ->
         cy, cx = int(rng.integers(gy)), int(rng.integers(gx))
         out[i] = img[cy * chip:(cy + 1) * chip, cx * chip:(cx + 1) * chip]
     return out
+
+
+def crop_tiles(img: np.ndarray, shapes, seed: int = 0):
+    """The uneven-tile batch as crops of one scene: for each (h, w, _) of
+    ``shapes`` a crop of that size (clamped to the scene) at a seeded random
+    position.  Returns (tiles, boxes) with boxes[i] = (y, x, h, w); the
+    tiles are contiguous copies."""
+    rng = np.random.default_rng(seed)
+    H, W = img.shape[:2]
+    tiles, boxes = [], []
+    for (h, w, _s) in shapes:
+        h, w = min(h, H), min(w, W)
+        y = int(rng.integers(0, H - h + 1))
+        x = int(rng.integers(0, W - w + 1))
+        tiles.append(np.ascontiguousarray(img[y:y + h, x:x + w]))
+        boxes.append((y, x, h, w))
+    return tiles, boxes
+
+
+def colour_cube() -> np.ndarray:
+    """Every 24-bit RGB colour once: a 4096 x 4096 x 3 uint8 image whose pixel
+    i = 4096 y + x has R = i >> 16, G = (i >> 8) & 255, B = i & 255."""
+    i = np.arange(1 << 24, dtype=np.uint32)
+    img = np.empty((1 << 24, 3), np.uint8)
+    img[:, 0] = i >> 16
+    img[:, 1] = (i >> 8) & 255
+    img[:, 2] = i & 255
+    return img.reshape(4096, 4096, 3)
