@@ -217,13 +217,45 @@ sil_status sil_label_batch(const sil_tile* tiles, int32_t n, sil_dtype dt,
 sil_status sil_label_batch_noalloc(const sil_tile* tiles, int32_t n, sil_dtype dt,
                                    const sil_params* p, sil_stream stream);
 
-/* Pick the persistent schedule (CTAs per SM, chip-order policy) for the
- * given batch by timing the candidates on `stream`; the result is cached in
- * ctx and used by later sil_label_batch calls with the same dt.  Blocks
- * until the timing is done.  best_ctas_per_sm may be NULL. */
+/* A schedule of the batched kernel (sil_label_batch). */
+typedef struct sil_tuning {
+  int32_t schedule;    /* 0: persistent CTAs, fixed chip stride;
+                          1: persistent CTAs taking chips from a work queue;
+                          2: one CTA per chip (the hardware hands chips to
+                             free slots) */
+  int32_t ctas_per_sm; /* CTAs per SM of schedules 0 and 1; 0 for schedule 2 */
+  int32_t threads;     /* threads per CTA: 256 (16 row bands) or 320 (20) */
+  float us;            /* time of one batch when tuned (0: not tuned) */
+} sil_tuning;
+
+/* Pick the batched kernel's schedule for the given batch by timing every
+ * candidate on `stream`: threads per CTA (256, 320) x {one CTA per chip;
+ * persistent CTAs with a work queue or a fixed stride at each number of
+ * CTAs per SM that fits}.  The winner is kept in ctx for the batch's class
+ * -- device name, dtype, H/S ranges narrowed or not, chip size, and the
+ * batch's tile count, chip count and chips per tile rounded down to powers
+ * of two -- so that later sil_label_batch calls of that class use it, and
+ * is saved to a cache file that sil_ctx_create loads: SIL_AUTOTUNE_CACHE if
+ * set (empty: no file), else $XDG_CACHE_HOME/sil-autotune.txt or
+ * $HOME/.cache/sil-autotune.txt (one text line per class).  Blocks until
+ * the timing is done.  best (may be NULL) receives the winner.  Untuned
+ * classes run one 256-thread CTA per chip.  (Pixels per thread, 16, and
+ * the row-staging depth, 3 slots, are fixed by the kernel's design.) */
+sil_status sil_autotune_ex(const sil_tile* tiles, int32_t n, sil_dtype dt,
+                           const sil_params* p, sil_ctx* ctx, sil_stream stream,
+                           sil_tuning* best);
+
+/* sil_autotune_ex reporting only the winner's CTAs per SM (0 when one CTA
+ * per chip won); best_ctas_per_sm may be NULL. */
 sil_status sil_autotune(const sil_tile* tiles, int32_t n, sil_dtype dt,
                         const sil_params* p, sil_ctx* ctx, sil_stream stream,
                         int32_t* best_ctas_per_sm);
+
+/* The schedule sil_label_batch would use for this batch (no launch);
+ * *tuned (may be NULL) = 1 if it comes from a tuning, 0 if the default. */
+sil_status sil_batch_tuning(const sil_tile* tiles, int32_t n, sil_dtype dt,
+                            const sil_params* p, sil_ctx* ctx, sil_tuning* out,
+                            int32_t* tuned);
 
 /* ---------------------------------------------------------------------
  * Served labeling: a continuous-batching request loop.  Requests arrive at

@@ -60,6 +60,14 @@ class sil_tile(ctypes.Structure):
     ]
 
 
+class sil_tuning(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("us", ctypes.c_float)]
+
+
+SCHED_STRIDE, SCHED_QUEUE, SCHED_PER_CHIP = 0, 1, 2
+
+
 class sil_server_config(ctypes.Structure):
     _fields_ = [
         ("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
@@ -95,6 +103,10 @@ _SIGS = {
     "sil_label_batch": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P, _P], _I32),
     "sil_autotune": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P, _P,
                       ctypes.POINTER(_I32)], _I32),
+    "sil_autotune_ex": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P, _P,
+                         ctypes.POINTER(sil_tuning)], _I32),
+    "sil_batch_tuning": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P,
+                          ctypes.POINTER(sil_tuning), ctypes.POINTER(_I32)], _I32),
     "sil_label_batch_noalloc": ([ctypes.POINTER(sil_tile), _I32, _I32, ctypes.POINTER(sil_params), _P], _I32),
     "sil_server_config_default": ([ctypes.POINTER(sil_server_config)], _I32),
     "sil_server_create": ([ctypes.POINTER(_P), ctypes.POINTER(sil_server_config), _I32,
@@ -301,12 +313,31 @@ def label_batch(ctx: Context, tiles, n: int, dt: int = SIL_U8, p=None, stream=No
                                _stream_handle(stream)))
 
 
-def autotune(ctx: Context, tiles, n: int, dt: int = SIL_U8, p=None, stream=None) -> int:
+def _tuning_dict(t: sil_tuning) -> dict:
+    return {"schedule": int(t.schedule), "ctas_per_sm": int(t.ctas_per_sm), "threads": int(t.threads),
+            "us": float(t.us)}
+
+
+def autotune(ctx: Context, tiles, n: int, dt: int = SIL_U8, p=None, stream=None) -> dict:
+    """Time every schedule of the batched kernel on this batch
+    (sil_autotune_ex); returns the winner as a dict (schedule, ctas_per_sm,
+    threads, us), which ctx then uses for batches of the same class."""
     pp = _as_params(p)
-    best = _I32(0)
-    check(_lib.sil_autotune(tiles, int(n), int(dt), ctypes.byref(pp), ctx.handle,
-                            _stream_handle(stream), ctypes.byref(best)))
-    return best.value
+    best = sil_tuning()
+    check(_lib.sil_autotune_ex(tiles, int(n), int(dt), ctypes.byref(pp), ctx.handle,
+                               _stream_handle(stream), ctypes.byref(best)))
+    return _tuning_dict(best)
+
+
+def batch_tuning(ctx: Context, tiles, n: int, dt: int = SIL_U8, p=None):
+    """The schedule sil_label_batch would use for this batch, and whether it
+    comes from a tuning: (dict, bool)."""
+    pp = _as_params(p)
+    t = sil_tuning()
+    tuned = _I32(0)
+    check(_lib.sil_batch_tuning(tiles, int(n), int(dt), ctypes.byref(pp), ctx.handle, ctypes.byref(t),
+                                ctypes.byref(tuned)))
+    return _tuning_dict(t), bool(tuned.value)
 
 
 def confusion(pred, ref, chip: int = 256, chip_conf: bool = False, stream=None):

@@ -10,7 +10,14 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <string>
+#include <sys/stat.h>
+#include <unistd.h>
 #include <vector>
 
 #include "sil.h"
@@ -50,18 +57,23 @@ __device__ __forceinline__ int find_tile(const int64_t* prefix, int n, int64_t k
   return lo;
 }
 
-template <int DT, bool HS, bool RESIDENT>
-__global__ void __launch_bounds__(kThreads, (DT == SIL_U8) ? 2 : 1)
+// Schedules of the batch kernel (chosen by the autotuner):
+//   kSchedStride  persistent CTAs, CTA c labels global chips c, c + grid, ...
+//   kSchedQueue   persistent CTAs taking the next chip from the queue head
+//   kSchedPerChip one CTA per chip (grid = total chips): the hardware block
+//                 scheduler hands chips to slots as they free up
+template <int DT, bool HS, bool RESIDENT, int NT>
+__global__ void __launch_bounds__(NT, (DT == SIL_U8) ? 2 : 1)
     k_label_batch(const Req* __restrict__ reqs, const int64_t* __restrict__ prefix,
                   int n, DevParams dp, int chip, unsigned long long* head,
-                  int dynamic) {
+                  int schedule) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   __shared__ uint8_t lut[256];
   __shared__ long long s_next;
   __shared__ __align__(16) ChipStat st_generic;
   const int64_t total = prefix[n];
   int64_t k = blockIdx.x;
-  if (dynamic) {
+  if (schedule == kSchedQueue) {
     if (threadIdx.x == 0) s_next = (long long)atomicAdd(head, 1ull);
     __syncthreads();
     k = s_next;
@@ -77,13 +89,15 @@ __global__ void __launch_bounds__(kThreads, (DT == SIL_U8) ? 2 : 1)
     } else {
       label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st_generic, lut);
     }
-    if (dynamic) {
+    if (schedule == kSchedQueue) {
       __syncthreads();  // everyone has read s_next
       if (threadIdx.x == 0) s_next = (long long)atomicAdd(head, 1ull);
       __syncthreads();
       k = s_next;
-    } else {
+    } else if (schedule == kSchedStride) {
       k += gridDim.x;
+    } else {
+      break;
     }
   }
 }
@@ -92,8 +106,12 @@ template <int DT, bool HS, bool RESIDENT>
 static cudaError_t launch_batch_t(const BatchLaunch& b, cudaStream_t s) {
   const size_t smem = RESIDENT ? resident_smem_bytes(DT, HS) : 0;
   k_batch_prologue<<<(b.n + 255) / 256, 256, 0, s>>>(b.reqs, b.n, b.head);
-  k_label_batch<DT, HS, RESIDENT><<<b.grid, kThreads, smem, s>>>(
-      b.reqs, b.prefix, b.n, b.dp, b.chip, b.head, b.dynamic);
+  if (b.threads == kThreadsWide)
+    k_label_batch<DT, HS, RESIDENT, kThreadsWide><<<b.grid, kThreadsWide, smem, s>>>(
+        b.reqs, b.prefix, b.n, b.dp, b.chip, b.head, b.schedule);
+  else
+    k_label_batch<DT, HS, RESIDENT, kThreadsNarrow><<<b.grid, kThreadsNarrow, smem, s>>>(
+        b.reqs, b.prefix, b.n, b.dp, b.chip, b.head, b.schedule);
   return cudaGetLastError();
 }
 
@@ -113,22 +131,30 @@ cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t s) {
 #undef SIL_DISPATCH
 }
 
-// Resident CTAs per SM the hardware allows for the batch kernel.
+// Resident CTAs per SM the hardware allows for the batch kernel (the same
+// for both CTA sizes: shared memory is laid out for the larger).
+template <int NT>
+static const void* batch_fn(int dt, bool hs, bool res) {
+#define SIL_F(DT, HS, R) reinterpret_cast<const void*>(k_label_batch<DT, HS, R, NT>)
+  if (dt == SIL_U8)
+    return hs ? (res ? SIL_F(SIL_U8, true, true) : SIL_F(SIL_U8, true, false))
+              : (res ? SIL_F(SIL_U8, false, true) : SIL_F(SIL_U8, false, false));
+  return hs ? (res ? SIL_F(SIL_U16, true, true) : SIL_F(SIL_U16, true, false))
+            : (res ? SIL_F(SIL_U16, false, true) : SIL_F(SIL_U16, false, false));
+#undef SIL_F
+}
+
 int batch_max_ctas_per_sm(int dt, bool hs, int chip) {
   int n = 0;
   const bool res = chip <= kResidentChip;
   const size_t smem = res ? resident_smem_bytes(dt, hs) : 0;
-  const void* f = nullptr;
-#define SIL_F(DT, HS, R) reinterpret_cast<const void*>(k_label_batch<DT, HS, R>)
-  if (dt == SIL_U8)
-    f = hs ? (res ? SIL_F(SIL_U8, true, true) : SIL_F(SIL_U8, true, false))
-           : (res ? SIL_F(SIL_U8, false, true) : SIL_F(SIL_U8, false, false));
-  else
-    f = hs ? (res ? SIL_F(SIL_U16, true, true) : SIL_F(SIL_U16, true, false))
-           : (res ? SIL_F(SIL_U16, false, true) : SIL_F(SIL_U16, false, false));
-#undef SIL_F
-  if (res) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem) != cudaSuccess || n < 1)
+  const void* fw = batch_fn<kThreadsWide>(dt, hs, res);
+  const void* fn = batch_fn<kThreadsNarrow>(dt, hs, res);
+  if (res) {
+    cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fw, kThreadsWide, smem) != cudaSuccess || n < 1)
     n = 1;
   return n;
 }
@@ -150,14 +176,24 @@ struct CachedGraph {
   uint64_t last_use = 0;
 };
 
+// A schedule of the batch kernel and its measured time.
+struct Tuning {
+  int schedule = kSchedPerChip;  // kSched*
+  int ctas = -1;                 // CTAs per SM of the persistent schedules (-1: all that fit)
+  int threads = kThreadsNarrow;  // threads per CTA
+  float us = 0.f;                // time of one batch when it was tuned
+};
+
 struct sil_ctx {
   int device = 0;
   int sms = 1;
+  std::string gpu;  // device name, part of every tuning key
   std::vector<CachedGraph> graphs;
   uint64_t tick = 0;
-  // tuning: CTAs per SM and queue policy, per dtype (-1 = not tuned)
-  int tuned_ctas[2] = {-1, -1};
-  int tuned_dynamic[2] = {1, 1};
+  // tuned schedules by batch class (tune_key); loaded from and saved to the
+  // cache file (empty path: not persisted)
+  std::map<std::string, Tuning> tuned;
+  std::string cache_path;
 };
 
 namespace {
@@ -209,14 +245,14 @@ sil_status build_batch(const sil_tile* tiles, int n, sil_dtype dt, const sil_par
 }
 
 std::vector<uint8_t> batch_key(const sil_tile* tiles, int n, sil_dtype dt, const sil_params* p,
-                               int grid, int dynamic) {
+                               int grid, int schedule, int threads) {
   sil_params def;
   if (!p) {
     sil_params_default(&def);
     p = &def;
   }
-  std::vector<uint8_t> k(sizeof(int) * 4 + sizeof(sil_params) + sizeof(sil_tile) * size_t(n));
-  int hdr[4] = {n, int(dt), grid, dynamic};
+  std::vector<uint8_t> k(sizeof(int) * 5 + sizeof(sil_params) + sizeof(sil_tile) * size_t(n));
+  int hdr[5] = {n, int(dt), grid, schedule, threads};
   memcpy(k.data(), hdr, sizeof(hdr));
   memcpy(k.data() + sizeof(hdr), p, sizeof(sil_params));
   memcpy(k.data() + sizeof(hdr) + sizeof(sil_params), tiles, sizeof(sil_tile) * size_t(n));
@@ -228,11 +264,86 @@ sil_status cuda_err(cudaError_t e, const char* what) {
   return SIL_ECUDA;
 }
 
+int log2_bucket(int64_t v) {
+  int b = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+// Class of a batch for the tuning cache: the device, the kernel instance
+// (dtype, H/S ranges, chip) and the batch's shape in powers of two (tiles,
+// chips, chips per tile); the best schedule depends on these, not on the
+// image contents.
+std::string tune_key(const sil_ctx* ctx, int dt, bool hs, int chip, int n, int64_t chips) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|dt%d|hs%d|chip%d|n%d|c%d|p%d", ctx->gpu.c_str(), dt, int(hs), chip,
+           log2_bucket(n), log2_bucket(chips), log2_bucket(chips / (n > 0 ? n : 1)));
+  std::string k(buf);
+  for (char& c : k)
+    if (c == ' ' || c == '\t' || c == '\n') c = '_';
+  return k;
+}
+
+// Cache file: SIL_AUTOTUNE_CACHE if set (empty: none), else
+// $XDG_CACHE_HOME/sil-autotune.txt or $HOME/.cache/sil-autotune.txt.
+std::string cache_file() {
+  const char* e = getenv("SIL_AUTOTUNE_CACHE");
+  if (e) return std::string(e);
+  const char* x = getenv("XDG_CACHE_HOME");
+  if (x && *x) return std::string(x) + "/sil-autotune.txt";
+  const char* h = getenv("HOME");
+  if (h && *h) return std::string(h) + "/.cache/sil-autotune.txt";
+  return std::string();
+}
+
+// One line per batch class: "<key> <schedule> <ctas> <threads> <us>".
+std::map<std::string, Tuning> load_tuning(const std::string& path) {
+  std::map<std::string, Tuning> m;
+  if (path.empty()) return m;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return m;
+  char key[256];
+  Tuning t;
+  while (fscanf(f, "%255s %d %d %d %f", key, &t.schedule, &t.ctas, &t.threads, &t.us) == 5) {
+    if (t.schedule < kSchedStride || t.schedule > kSchedPerChip) continue;
+    if (t.threads != kThreadsNarrow && t.threads != kThreadsWide) continue;
+    m[key] = t;
+  }
+  fclose(f);
+  return m;
+}
+
+// Merges the context's entries into the file (written whole to a temporary
+// file, then renamed over it).  Failing to write is not an error of the
+// tuning itself.
+void save_tuning(const sil_ctx* ctx) {
+  const std::string& path = ctx->cache_path;
+  if (path.empty()) return;
+  std::map<std::string, Tuning> m = load_tuning(path);
+  for (const auto& kv : ctx->tuned) m[kv.first] = kv.second;
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
+  const std::string tmp = path + ".tmp" + std::to_string(long(getpid()));
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  for (const auto& kv : m)
+    fprintf(f, "%s %d %d %d %.3f\n", kv.first.c_str(), kv.second.schedule, kv.second.ctas,
+            kv.second.threads, kv.second.us);
+  const bool ok = fclose(f) == 0;
+  if (ok)
+    rename(tmp.c_str(), path.c_str());
+  else
+    remove(tmp.c_str());
+}
+
 // Uploads descriptors (synchronously) and records prologue + persistent
 // kernel into a graph.
 sil_status make_graph(sil_ctx* ctx, const std::vector<Req>& reqs,
                       const std::vector<int64_t>& prefix, int dt, const DevParams& dp,
-                      int chip, int grid, int dynamic, CachedGraph& g) {
+                      int chip, int grid, int schedule, int threads, CachedGraph& g) {
   const int n = int(reqs.size());
   cudaError_t e;
   if ((e = cudaMalloc(&g.d_reqs, sizeof(Req) * n)) != cudaSuccess ||
@@ -253,7 +364,7 @@ sil_status make_graph(sil_ctx* ctx, const std::vector<Req>& reqs,
     free_graph(g);
     return cuda_err(e, "capture stream");
   }
-  BatchLaunch b{g.d_reqs, g.d_prefix, n, dt, dp, chip, g.d_head, grid, dynamic};
+  BatchLaunch b{g.d_reqs, g.d_prefix, n, dt, dp, chip, g.d_head, grid, schedule, threads};
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t le = launch_batch(b, cs);
@@ -267,6 +378,75 @@ sil_status make_graph(sil_ctx* ctx, const std::vector<Req>& reqs,
     return cuda_err(e, "batch graph capture");
   }
   (void)ctx;
+  return SIL_OK;
+}
+
+// The schedule a batch of this class runs with: the tuned one if there is
+// one, else one CTA per chip of 256 threads.
+Tuning batch_tuning(const sil_ctx* ctx, const std::string& key, int maxc) {
+  auto it = ctx->tuned.find(key);
+  Tuning t = it != ctx->tuned.end() ? it->second : Tuning();
+  t.ctas = t.ctas > 0 ? std::min(t.ctas, maxc) : maxc;
+  return t;
+}
+
+// Records (if needed) and replays the batch's graph for tuning t.
+sil_status run_batch(const sil_tile* tiles, int32_t n, sil_dtype dt, const sil_params* p,
+                     sil_ctx* ctx, cudaStream_t stream, const DevParams& dp,
+                     const std::vector<Req>& reqs, const std::vector<int64_t>& prefix,
+                     const Tuning& t) {
+  const int chip = p ? p->chip : 256;
+  const int64_t total = prefix[n];
+  int schedule = t.schedule;
+  if (schedule == kSchedPerChip && total > int64_t(0x7fffffff)) schedule = kSchedQueue;
+  const int grid = schedule == kSchedPerChip ? int(total)
+                                             : int(std::min<int64_t>(total, int64_t(ctx->sms) * t.ctas));
+  std::vector<uint8_t> key = batch_key(tiles, n, dt, p, grid, schedule, t.threads);
+  CachedGraph* hit = nullptr;
+  for (auto& g : ctx->graphs)
+    if (g.key == key) hit = &g;
+  if (!hit) {
+    CachedGraph g;
+    sil_status st = make_graph(ctx, reqs, prefix, dt, dp, chip, grid, schedule, t.threads, g);
+    if (st != SIL_OK) return st;
+    g.key = std::move(key);
+    if (ctx->graphs.size() >= 16) {
+      auto old = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                  [](const CachedGraph& a, const CachedGraph& b) {
+                                    return a.last_use < b.last_use;
+                                  });
+      free_graph(*old);
+      *old = std::move(g);
+      hit = &*old;
+    } else {
+      ctx->graphs.push_back(std::move(g));
+      hit = &ctx->graphs.back();
+    }
+  }
+  hit->last_use = ++ctx->tick;
+  cudaError_t e = cudaGraphLaunch(hit->exec, stream);
+  if (e != cudaSuccess) return cuda_err(e, "sil_label_batch: graph launch");
+  return SIL_OK;
+}
+
+// Shared argument checks and descriptor building of the batch entry points.
+sil_status prepare_batch(const char* who, const sil_tile* tiles, int32_t n, sil_dtype dt,
+                         const sil_params* p, sil_ctx* ctx, DevParams* dp, std::vector<Req>& reqs,
+                         std::vector<int64_t>& prefix, std::string* key, int* maxc) {
+  if (!ctx || !tiles || n < 1) {
+    set_error("%s: NULL context/tiles or n < 1", who);
+    return SIL_EINVAL;
+  }
+  sil_status st = derive_params(p, dp);
+  if (st != SIL_OK) return st;
+  if (dt != SIL_U8 && dt != SIL_U16) {
+    set_error("%s: dtype %d", who, int(dt));
+    return SIL_EINVAL;
+  }
+  if ((st = build_batch(tiles, n, dt, p, reqs, prefix)) != SIL_OK) return st;
+  const int chip = p ? p->chip : 256;
+  *maxc = batch_max_ctas_per_sm(dt, dp->need_hs != 0, chip);
+  *key = tune_key(ctx, int(dt), dp->need_hs != 0, chip, n, prefix[n]);
   return SIL_OK;
 }
 
@@ -288,6 +468,11 @@ sil_status sil_ctx_create(sil_ctx** ctx, int device) {
   c->device = device;
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (c->sms < 1) c->sms = 1;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) c->gpu = prop.name;
+  if (c->gpu.empty()) c->gpu = "gpu";
+  c->cache_path = cache_file();
+  c->tuned = load_tuning(c->cache_path);
   *ctx = c;
   return SIL_OK;
 }
@@ -303,109 +488,118 @@ void sil_ctx_destroy(sil_ctx* ctx) {
 
 sil_status sil_label_batch(const sil_tile* tiles, int32_t n, sil_dtype dt,
                            const sil_params* p, sil_ctx* ctx, sil_stream stream) {
-  if (!ctx || !tiles || n < 1) {
-    set_error("sil_label_batch: NULL context/tiles or n < 1");
+  if (!ctx) {
+    set_error("sil_label_batch: NULL context");
     return SIL_EINVAL;
   }
   DeviceGuard guard(ctx->device);
   DevParams dp;
-  sil_status st = derive_params(p, &dp);
-  if (st != SIL_OK) return st;
-  if (dt != SIL_U8 && dt != SIL_U16) {
-    set_error("dtype %d", int(dt));
-    return SIL_EINVAL;
-  }
-  const int chip = p ? p->chip : 256;
-  const int maxc = batch_max_ctas_per_sm(dt, dp.need_hs != 0, chip);
-  const int ti = dt == SIL_U8 ? 0 : 1;
-  const int cps = ctx->tuned_ctas[ti] > 0 ? std::min(ctx->tuned_ctas[ti], maxc) : maxc;
-  const int dynamic = ctx->tuned_dynamic[ti];
   std::vector<Req> reqs;
   std::vector<int64_t> prefix;
-  if ((st = build_batch(tiles, n, dt, p, reqs, prefix)) != SIL_OK) return st;
-  const int64_t total = prefix[n];
-  const int grid = int(std::min<int64_t>(total, int64_t(ctx->sms) * cps));
-  std::vector<uint8_t> key = batch_key(tiles, n, dt, p, grid, dynamic);
-  CachedGraph* hit = nullptr;
-  for (auto& g : ctx->graphs)
-    if (g.key == key) hit = &g;
-  if (!hit) {
-    CachedGraph g;
-    if ((st = make_graph(ctx, reqs, prefix, dt, dp, chip, grid, dynamic, g)) != SIL_OK) return st;
-    g.key = std::move(key);
-    if (ctx->graphs.size() >= 16) {
-      auto old = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
-                                  [](const CachedGraph& a, const CachedGraph& b) {
-                                    return a.last_use < b.last_use;
-                                  });
-      free_graph(*old);
-      *old = std::move(g);
-      hit = &*old;
-    } else {
-      ctx->graphs.push_back(std::move(g));
-      hit = &ctx->graphs.back();
+  std::string key;
+  int maxc = 1;
+  sil_status st = prepare_batch("sil_label_batch", tiles, n, dt, p, ctx, &dp, reqs, prefix, &key, &maxc);
+  if (st != SIL_OK) return st;
+  return run_batch(tiles, n, dt, p, ctx, reinterpret_cast<cudaStream_t>(stream), dp, reqs, prefix,
+                   batch_tuning(ctx, key, maxc));
+}
+
+sil_status sil_batch_tuning(const sil_tile* tiles, int32_t n, sil_dtype dt, const sil_params* p,
+                            sil_ctx* ctx, sil_tuning* out, int32_t* tuned) {
+  if (!ctx || !out) {
+    set_error("sil_batch_tuning: NULL context or output");
+    return SIL_EINVAL;
+  }
+  DeviceGuard guard(ctx->device);
+  DevParams dp;
+  std::vector<Req> reqs;
+  std::vector<int64_t> prefix;
+  std::string key;
+  int maxc = 1;
+  sil_status st = prepare_batch("sil_batch_tuning", tiles, n, dt, p, ctx, &dp, reqs, prefix, &key, &maxc);
+  if (st != SIL_OK) return st;
+  const Tuning t = batch_tuning(ctx, key, maxc);
+  out->schedule = t.schedule;
+  out->ctas_per_sm = t.schedule == kSchedPerChip ? 0 : t.ctas;
+  out->threads = t.threads;
+  out->us = t.us;
+  if (tuned) *tuned = ctx->tuned.count(key) ? 1 : 0;
+  return SIL_OK;
+}
+
+sil_status sil_autotune_ex(const sil_tile* tiles, int32_t n, sil_dtype dt, const sil_params* p,
+                           sil_ctx* ctx, sil_stream stream, sil_tuning* best_out) {
+  if (!ctx) {
+    set_error("sil_autotune: NULL context");
+    return SIL_EINVAL;
+  }
+  DeviceGuard guard(ctx->device);
+  DevParams dp;
+  std::vector<Req> reqs;
+  std::vector<int64_t> prefix;
+  std::string key;
+  int maxc = 1;
+  sil_status st = prepare_batch("sil_autotune", tiles, n, dt, p, ctx, &dp, reqs, prefix, &key, &maxc);
+  if (st != SIL_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // candidates: for each CTA size, one CTA per chip and the persistent
+  // schedules (queue, stride) at every CTAs-per-SM count that fits
+  std::vector<Tuning> cand;
+  for (int threads : {kThreadsNarrow, kThreadsWide}) {
+    Tuning t;
+    t.threads = threads;
+    t.schedule = kSchedPerChip;
+    t.ctas = maxc;
+    cand.push_back(t);
+    for (int c = 1; c <= maxc; ++c) {
+      t.ctas = c;
+      t.schedule = kSchedQueue;
+      cand.push_back(t);
+      t.schedule = kSchedStride;
+      cand.push_back(t);
     }
   }
-  hit->last_use = ++ctx->tick;
-  cudaError_t e = cudaGraphLaunch(hit->exec, reinterpret_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_err(e, "sil_label_batch: graph launch");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  Tuning best;
+  best.us = 1e30f;
+  for (Tuning& t : cand) {
+    // warm-up (also records the graph), then the median of 3 timed runs
+    if ((st = run_batch(tiles, n, dt, p, ctx, s, dp, reqs, prefix, t)) != SIL_OK) break;
+    float ms[3];
+    for (int rep = 0; rep < 3 && st == SIL_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      st = run_batch(tiles, n, dt, p, ctx, s, dp, reqs, prefix, t);
+      cudaEventRecord(e1, s);
+      if (st == SIL_OK && cudaEventSynchronize(e1) != cudaSuccess)
+        st = cuda_err(cudaGetLastError(), "sil_autotune: timing");
+      if (st == SIL_OK) cudaEventElapsedTime(&ms[rep], e0, e1);
+    }
+    if (st != SIL_OK) break;
+    std::sort(ms, ms + 3);
+    t.us = ms[1] * 1000.f;
+    if (t.us < best.us) best = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SIL_OK) return st;
+  ctx->tuned[key] = best;
+  save_tuning(ctx);
+  if (best_out) {
+    best_out->schedule = best.schedule;
+    best_out->ctas_per_sm = best.schedule == kSchedPerChip ? 0 : best.ctas;
+    best_out->threads = best.threads;
+    best_out->us = best.us;
+  }
   return SIL_OK;
 }
 
 sil_status sil_autotune(const sil_tile* tiles, int32_t n, sil_dtype dt, const sil_params* p,
                         sil_ctx* ctx, sil_stream stream, int32_t* best_ctas_per_sm) {
-  if (!ctx || !tiles || n < 1) {
-    set_error("sil_autotune: NULL context/tiles or n < 1");
-    return SIL_EINVAL;
-  }
-  DeviceGuard guard(ctx->device);
-  DevParams dp;
-  sil_status st = derive_params(p, &dp);
-  if (st != SIL_OK) return st;
-  if (dt != SIL_U8 && dt != SIL_U16) {
-    set_error("dtype %d", int(dt));
-    return SIL_EINVAL;
-  }
-  const int chip = p ? p->chip : 256;
-  const int maxc = batch_max_ctas_per_sm(dt, dp.need_hs != 0, chip);
-  const int ti = dt == SIL_U8 ? 0 : 1;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_c = maxc, best_d = 1;
-  for (int c = 1; c <= maxc; ++c) {
-    for (int d = 0; d <= 1; ++d) {
-      ctx->tuned_ctas[ti] = c;
-      ctx->tuned_dynamic[ti] = d;
-      // warm-up (also builds the graph), then the median of 3 timed runs
-      if ((st = sil_label_batch(tiles, n, dt, p, ctx, stream)) != SIL_OK) goto done;
-      float t[3];
-      for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, s);
-        if ((st = sil_label_batch(tiles, n, dt, p, ctx, stream)) != SIL_OK) goto done;
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          st = cuda_err(cudaGetLastError(), "sil_autotune: timing");
-          goto done;
-        }
-        cudaEventElapsedTime(&t[rep], e0, e1);
-      }
-      std::sort(t, t + 3);
-      if (t[1] < best) {
-        best = t[1];
-        best_c = c;
-        best_d = d;
-      }
-    }
-  }
-  ctx->tuned_ctas[ti] = best_c;
-  ctx->tuned_dynamic[ti] = best_d;
-  if (best_ctas_per_sm) *best_ctas_per_sm = best_c;
-done:
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  sil_tuning t;
+  const sil_status st = sil_autotune_ex(tiles, n, dt, p, ctx, stream, &t);
+  if (st == SIL_OK && best_ctas_per_sm) *best_ctas_per_sm = t.ctas_per_sm;
   return st;
 }
 

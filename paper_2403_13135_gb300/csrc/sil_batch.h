@@ -16,8 +16,11 @@ struct BatchLaunch {
   int chip;
   unsigned long long* head;  // device work-queue head (zeroed by the prologue)
   int grid;
-  int dynamic;              // 1: CTAs take chips from the queue head; 0: fixed stride
+  int schedule;             // kSched*: how CTAs get their chips
+  int threads = kThreadsNarrow;  // threads per CTA: kThreadsNarrow or kThreadsWide
 };
+
+enum { kSchedStride = 0, kSchedQueue = 1, kSchedPerChip = 2 };
 
 // Enqueues the prologue (zero counts, reset head) and the persistent kernel.
 // batch_max_ctas_per_sm() must have been called once for the same (dt, H/S,

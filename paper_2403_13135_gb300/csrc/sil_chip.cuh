@@ -1,6 +1,6 @@
 // sil_chip.cuh -- the fused per-chip labeler (device code).
 //
-// One CTA of 320 threads (20 half-warps) labels one chip of at most
+// One CTA of 256 threads (16 half-warps) labels one chip of at most
 // 256 x 256 pixels; a persistent CTA loops over chips.
 //
 //   pass 1  each half-warp owns a band of rows, each lane 16 columns of them.
@@ -39,8 +39,12 @@
 
 namespace sil {
 
-constexpr int kWarps = kThreads / 32;
-constexpr int kBands = kThreads / 16;  // one row band per half-warp
+constexpr int kMaxWarps = kMaxThreads / 32;
+constexpr int kMaxBands = kMaxThreads / 16;  // one row band per half-warp
+// warps and bands of the running CTA (blockDim.x is 256 or 320)
+__device__ __forceinline__ int n_warps() { return int(blockDim.x) >> 5; }
+__device__ __forceinline__ int n_bands() { return int(blockDim.x) >> 4; }
+constexpr int kBinWarps = 256 / 32;  // warps whose threads own a histogram bin
 constexpr int kPlaneStride = 256;
 #ifndef SIL_RING
 #define SIL_RING 3
@@ -52,17 +56,17 @@ constexpr int kLanePx = 16;
 // that nothing reads: lanes past a narrow chip's last column count there.
 struct ChipStat {
   uint32_t hist[256 + 32];
-  uint32_t red[kWarps][4];
-  uint32_t nod[kWarps];
+  uint32_t red[kMaxWarps][4];
+  uint32_t nod[kMaxWarps];
   int32_t stat[8];
 };
 // Scratch of the block-wide Otsu search.
 struct alignas(16) StatScratch {
-  uint32_t wc[kWarps], ws[kWarps];
-  uint64_t bnum_lo[kWarps];
-  uint32_t bnum_hi[kWarps], bden[kWarps];
-  int32_t bt[kWarps], lo[kWarps], hi[kWarps];
-  float fmax[kWarps];
+  uint32_t wc[kMaxWarps], ws[kMaxWarps];
+  uint64_t bnum_lo[kMaxWarps];
+  uint32_t bnum_hi[kMaxWarps], bden[kMaxWarps];
+  int32_t bt[kMaxWarps], lo[kMaxWarps], hi[kMaxWarps];
+  float fmax[kMaxWarps];
   uint32_t n0;
 };
 
@@ -79,7 +83,7 @@ template <int BPP, bool FLAGS>
 struct ChipSmemT {
   ChipStat st;
   StatScratch sc;
-  alignas(16) uint8_t ring[kBands][kRing][Slot<BPP>::kBytes];
+  alignas(16) uint8_t ring[kMaxBands][kRing][Slot<BPP>::kBytes];
   alignas(16) uint8_t vf[256 * kPlaneStride];  // filtered V, plane order
   // per row, per lane: 16 nibbles (bits 0-2 class mask of the H/S ranges,
   // bit 3 nodata); uint16 and H/S-narrowed variants only
@@ -98,6 +102,12 @@ __device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
 // a * b + c with b a runtime kernel parameter: stays an integer multiply-add,
 // which issues on the multiply-add pipe, beside the min/max/permute pipe.
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) { return a * b + c; }
+// Four bytes (each < 256) packed into a word, a | b << 8 | c << 16 | d << 24,
+// as multiply-adds.
+__device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                          const DevParams& dp) {
+  return imad(d, dp.sh24, imad(c, dp.sh16, imad(b, dp.sh8, a)));
+}
 // a + b + c - x - y, exact modulo 2^32 (the two subtractions as multiply-adds)
 __device__ __forceinline__ uint32_t sum3m2(uint32_t a, uint32_t b, uint32_t c, uint32_t x,
                                            uint32_t y, const DevParams& dp) {
@@ -125,20 +135,39 @@ __device__ __forceinline__ uint32_t u16_to_v8(uint32_t x, const DevParams& dp) {
 // (cp.async.wait_group) and the half-warp then synchronises, so no thread
 // spins on a flag.
 // ---------------------------------------------------------------------------
+// One 16-byte asynchronous copy when pred is nonzero (a predicated
+// instruction, no branch).
+__device__ __forceinline__ void cp16_if(uint32_t dst, uintptr_t src, uint32_t pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t"
+      "@p cp.async.cg.shared.global [%0], [%1], 16;\n\t}" ::"r"(dst),
+      "l"(src), "r"(pred) : "memory");
+}
 template <int SLOT_BYTES>
 __device__ __forceinline__ void copy_row_async(uint8_t* slot, const uint8_t* rowptr,
-                                               int row_bytes, int q) {
+                                               int row_bytes, int q, bool go) {
   const uintptr_t a = reinterpret_cast<uintptr_t>(rowptr);
   const uintptr_t A = a & ~uintptr_t(15);
-  const int nvec = int(((a + uintptr_t(row_bytes) + 15) & ~uintptr_t(15)) - A) >> 4;
+  const int nvec = go ? int(((a + uintptr_t(row_bytes) + 15) & ~uintptr_t(15)) - A) >> 4 : 0;
   const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(slot));
 #pragma unroll
   for (int t = 0; t < (SLOT_BYTES / 16 + 15) / 16; ++t) {
     const int v = q + 16 * t;
-    if (v < nvec)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                   ::"r"(dst + 16u * uint32_t(v)), "l"(A + 16u * uintptr_t(v)) : "memory");
+    cp16_if(dst + 16u * uint32_t(v), A + 16u * uintptr_t(v), v < nvec);
   }
+}
+// A full-width row (256 px): every lane copies the same number of blocks,
+// and the one extra block of a row that does not start on a 16-byte boundary
+// (m != 0) is lane 0's.
+template <int BPP>
+__device__ __forceinline__ void copy_row_full(uint8_t* slot, const uint8_t* rowptr, uint32_t m,
+                                              int q, bool go) {
+  constexpr int kBlocks = BPP * 256 / 16;  // a multiple of 16
+  const uintptr_t A = (reinterpret_cast<uintptr_t>(rowptr) & ~uintptr_t(15)) + 16u * uintptr_t(q);
+  const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(slot)) + 16u * uint32_t(q);
+#pragma unroll
+  for (int t = 0; t < kBlocks / 16; ++t) cp16_if(dst + 256u * uint32_t(t), A + 256u * uintptr_t(t), go);
+  cp16_if(dst + 16u * kBlocks, A + 16u * kBlocks, go && q == 0 && m != 0);
 }
 __device__ __forceinline__ void commit_rows() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -382,8 +411,10 @@ __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const
   if (!kFlags && FULL) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
+      // low lane: byte 1 by a permute; high lane: byte 3 = the high word of
+      // out * 2^8, a multiply (the two go to different pipes)
       atomicAdd(&hist[__byte_perm(out[i], 0, 0x4441)], 1u);
-      atomicAdd(&hist[__byte_perm(out[i], 0, 0x4443)], 1u);
+      atomicAdd(&hist[__umulhi(out[i], dp.sh8)], 1u);
     }
   } else if (!kFlags) {
     // a chip narrower than 256: the same adds in every lane (no branch that
@@ -421,71 +452,95 @@ __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const
   }
 }
 
+// The rows one half-warp band streams for one chip: output rows [r0, r1)
+// of a chip of h rows and w columns whose pixel (0, 0) is at chip0; streamed
+// row k (k = 0 .. r1 - r0 + 1) is chip row clamp(r0 + k - 1, 0, h - 1).
+struct Band {
+  const uint8_t* chip0;
+  int64_t pitch;
+  int h, w, r0, r1;
+};
+
+__device__ __forceinline__ const uint8_t* band_row(const Band& b, int k) {
+  return b.chip0 + int64_t(min(max(b.r0 + k - 1, 0), b.h - 1)) * b.pitch;
+}
+
+// Copy streamed row k into slot when go (predicated, no branch); m = the
+// row's offset from the 16-byte block below it.  FULL: the chip is 256 wide.
+template <int BPP, bool FULL>
+__device__ __forceinline__ void band_issue(const Band& b, uint8_t* slot, int k, uint32_t& m,
+                                           bool go, int q) {
+  const uint8_t* src = band_row(b, k);
+  m = uint32_t(reinterpret_cast<uintptr_t>(src)) & 15u;
+  if (FULL)
+    copy_row_full<BPP>(slot, src, m, q, go);
+  else
+    copy_row_async<Slot<BPP>::kBytes>(slot, src, BPP * b.w, q, go);
+}
+
 // Pass 1 of one half-warp's band: output rows r0..r1-1 of the chip.  The
-// band streams rows e(k) = clamp(r0 + k - 1, 0, h - 1), k = 0 .. r1 - r0 + 1,
-// through its ring of kRing row slots, kRing - 1 rows ahead of the one being
-// decoded.  FULL: every lane has 16 columns (chip width 256).  A4: every row
-// of the chip starts on a 4-byte boundary.
+// band streams its rows through its ring of kRing = 3 row slots: step k
+// waits for streamed row k, decodes it from slot k mod 3 and refills that
+// slot with row k + 3.  The row loop is unrolled by three so that the window
+// rows (y-1, y, y+1) rotate through three register sets and each slot index
+// is a constant.  FULL: every lane has 16 columns (chip width 256).  A4:
+// every row of the chip starts on a 4-byte boundary.
 template <int DT, bool HS, bool FULL, bool A4, class SM>
-__device__ __forceinline__ void band_pass1(const uint8_t* img, int64_t pitch, int64_t y0,
-                                           int64_t x0, int h, int w, int r0, int r1,
-                                           const DevParams& dp, SM& sm, uint32_t& n_nodata) {
+__device__ __forceinline__ void band_pass1(const Band& b, const DevParams& dp, SM& sm,
+                                           uint32_t& n_nodata) {
   constexpr int BPP = Px<DT>::BPP;
   constexpr bool kFlags = HS || DT == SIL_U16;
   constexpr int SB = Slot<BPP>::kBytes;
+  static_assert(kRing == 3, "the row loop is unrolled by the ring size");
   const int lane = threadIdx.x & 31, band = threadIdx.x >> 4;
   const int q = lane & 15;
   const uint32_t hmask = 0xFFFFu << (lane & 16);
+  const int w = b.w, r0 = b.r0, r1 = b.r1;
   const int nvalid = FULL ? 16 : min(max(w - 16 * q, 0), 16);
   const bool use_median = dp.filter && dp.median;
-  const int row_bytes = BPP * w;
-  const int nrows = r1 - r0 + 2;
-  uint8_t* ring = sm.ring[band][0];
-  const uint8_t* chip0 = img + x0 * BPP + y0 * pitch;
-  // copy cursor: row index and pointer of the next row to copy
-  int cy = max(r0 - 1, 0);
-  const uint8_t* cp = chip0 + int64_t(cy) * pitch;
-  // decode cursor
-  int dy = cy;
-  const uint8_t* dptr = cp;
-#pragma unroll
-  for (int k = 0; k < kRing; ++k) {
-    if (k < nrows) copy_row_async<SB>(ring + k * SB, cp, row_bytes, q);
-    commit_rows();
-    const int ny = min(r0 + k, h - 1);  // e(k + 1)
-    if (ny != cy) cp += pitch;
-    cy = ny;
-  }
-  int k = 0, slot_i = 0;
-  // one ring step: decode row e(k) into B, refill its slot with e(k + kRing)
-  auto step = [&](RowBuf& B) {
-    uint8_t* slot = ring + slot_i * SB;
-    wait_rows<kRing - 1>();  // this lane's copies of row e(k) have landed
+  const int nrows = r1 - r0 + 2;  // streamed rows 0 .. r1 - r0 + 1
+  uint8_t* const s0 = sm.ring[band][0];
+  uint8_t* const s1 = s0 + SB;
+  uint8_t* const s2 = s1 + SB;
+  uint32_t m0, m1, m2;
+  band_issue<BPP, FULL>(b, s0, 0, m0, true, q);
+  commit_rows();
+  band_issue<BPP, FULL>(b, s1, 1, m1, true, q);
+  commit_rows();
+  band_issue<BPP, FULL>(b, s2, 2, m2, nrows > 2, q);
+  commit_rows();
+  // step k: decode row k from its slot into B, refill the slot with row k + 3
+  auto step = [&](RowBuf& B, uint8_t* slot, uint32_t& m, int k) {
+    wait_rows<kRing - 1>();  // this lane's copies of row k have landed
     __syncwarp(hmask);       // ... and every other lane's of the band
-    decode_row<DT, HS, A4>(slot, int(reinterpret_cast<uintptr_t>(dptr) & 15), q, nvalid, dp, B.v, B.f);
+    decode_row<DT, HS, A4>(slot, int(m), q, nvalid, dp, B.v, B.f);
     __syncwarp(hmask);  // the slot is free again
-    if (k + kRing < nrows) copy_row_async<SB>(slot, cp, row_bytes, q);
+    band_issue<BPP, FULL>(b, slot, k + kRing, m, k + kRing < nrows, q);
     commit_rows();
-    const int ny = min(r0 + k + kRing, h - 1);  // e(k + kRing + 1)
-    if (ny != cy) cp += pitch;
-    cy = ny;
-    const int nd = min(r0 + k, h - 1);  // e(k + 1)
-    if (nd != dy) dptr += pitch;
-    dy = nd;
     edge_words(B.v, q, w, hmask, B.eL, B.eR);
-    ++k;
-    slot_i = (slot_i == kRing - 1) ? 0 : slot_i + 1;
   };
-  RowBuf M, Z, P;
-  step(M);
-  step(Z);
-  for (int y = r0; y < r1; ++y) {
-    step(P);
-    emit_row<kFlags, DT, FULL>(M, Z, P, y, q, nvalid, use_median, dp, sm, n_nodata);
-    M = Z;
-    Z = P;
+  RowBuf B0, B1, B2;
+  step(B0, s0, m0, 0);
+  step(B1, s1, m1, 1);
+  int y = r0, k = 2;
+  for (; y + 3 <= r1; y += 3, k += 3) {
+    step(B2, s2, m2, k);
+    emit_row<kFlags, DT, FULL>(B0, B1, B2, y, q, nvalid, use_median, dp, sm, n_nodata);
+    step(B0, s0, m0, k + 1);
+    emit_row<kFlags, DT, FULL>(B1, B2, B0, y + 1, q, nvalid, use_median, dp, sm, n_nodata);
+    step(B1, s1, m1, k + 2);
+    emit_row<kFlags, DT, FULL>(B2, B0, B1, y + 2, q, nvalid, use_median, dp, sm, n_nodata);
   }
-  wait_rows<0>();
+  if (y < r1) {
+    step(B2, s2, m2, k);
+    emit_row<kFlags, DT, FULL>(B0, B1, B2, y, q, nvalid, use_median, dp, sm, n_nodata);
+    if (y + 1 < r1) {
+      step(B0, s0, m0, k + 1);
+      emit_row<kFlags, DT, FULL>(B1, B2, B0, y + 1, q, nvalid, use_median, dp, sm, n_nodata);
+    }
+  }
+  // every copy this band issued for the chip has been waited for (the
+  // groups committed after the last row's copy are empty)
 }
 
 // ---------------------------------------------------------------------------
@@ -634,10 +689,12 @@ __device__ __forceinline__ void chip_stats_block(ChipStat& st, StatScratch& sc,
     sc.hi[wid] = nz ? wid * 32 + 31 - __clz(nz) : -1;
   }
   __syncthreads();
+  // only the first 8 warps own histogram bins (threads 256.. contribute
+  // nothing to the sums, the extremes or the scores)
   uint32_t ST = 0, pc = 0, ps = 0;
   int lo = 256, hi = -1;
 #pragma unroll
-  for (int k = 0; k < kWarps; ++k) {
+  for (int k = 0; k < kBinWarps; ++k) {
     if (k < wid) {
       pc += sc.wc[k];
       ps += sc.ws[k];
@@ -678,7 +735,7 @@ __device__ __forceinline__ void chip_stats_block(ChipStat& st, StatScratch& sc,
   __syncthreads();
   float M = -1.f;
 #pragma unroll
-  for (int k = 0; k < kWarps; ++k) M = fmaxf(M, sc.fmax[k]);
+  for (int k = 0; k < kBinWarps; ++k) M = fmaxf(M, sc.fmax[k]);
   const bool cand = t >= 0 && f >= M * (1.0f - 4e-6f);
   const int ncand = __syncthreads_count(cand);
   if (ncand <= 1) {
@@ -720,7 +777,7 @@ __device__ __forceinline__ void chip_stats_block(ChipStat& st, StatScratch& sc,
   }
   __syncthreads();
   if (wid == 0) {
-    const bool own = lane < kWarps;
+    const bool own = lane < kBinWarps;
     nlo = own ? sc.bnum_lo[lane] : 0;
     nhi = own ? sc.bnum_hi[lane] : 0;
     den = own ? sc.bden[lane] : 0;
@@ -821,13 +878,35 @@ __device__ __forceinline__ void store_row16(uint8_t* dst, int nvalid, uint4 lab)
     if (j < nvalid) dst[j] = uint8_t(wv[j >> 2] >> (8 * (j & 3)));
 }
 
-template <int DT, bool HS, class SM>
+// Store of a lane's 16 labels.  STORE: every label row of the chip starts
+// on a 16-byte (16) or 4-byte (4) boundary, or neither (1); known per chip,
+// so the choice is not made per row.  Lanes with fewer than 16 columns left
+// (the right edge of a narrow chip) store bytes.
+template <int STORE>
+__device__ __forceinline__ void store_labels(uint8_t* dst, int nvalid, uint4 lab) {
+  if (STORE == 16 && nvalid == 16) {
+    *reinterpret_cast<uint4*>(dst) = lab;
+  } else if (STORE == 4 && nvalid == 16) {
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    d[0] = lab.x;
+    d[1] = lab.y;
+    d[2] = lab.z;
+    d[3] = lab.w;
+  } else {
+    const uint32_t wv[4] = {lab.x, lab.y, lab.z, lab.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < nvalid) dst[j] = uint8_t(wv[j >> 2] >> (8 * (j & 3)));
+  }
+}
+
+template <int DT, bool HS, int STORE, bool FULL, class SM>
 __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int64_t y0, int64_t x0,
                                            int w, int r0, int r1, const uint8_t* lut, const SM& sm,
                                            uint32_t* cnt, const DevParams& dp) {
   constexpr bool kFlags = HS || DT == SIL_U16;
   const int q = threadIdx.x & 15;
-  const int nvalid = min(max(w - 16 * q, 0), 16);
+  const int nvalid = FULL ? 16 : min(max(w - 16 * q, 0), 16);
   if (nvalid == 0) return;
   uint8_t* dst = labels ? labels + (y0 + r0) * lpitch + x0 + 16 * q : nullptr;
   for (int y = r0; y < r1; ++y) {
@@ -840,7 +919,7 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
       l[2 * k] = lut[__byte_perm(p[k], 0, 0x4440)];
       l[2 * k + 1] = lut[__byte_perm(p[k], 0, 0x4441)];
       l[2 * k + 8] = lut[__byte_perm(p[k], 0, 0x4442)];
-      l[2 * k + 9] = lut[__byte_perm(p[k], 0, 0x4443)];
+      l[2 * k + 9] = lut[__umulhi(p[k], dp.sh8)];  // byte 3
     }
     if (kFlags) {
       const uint32_t f0 = sm.flags[y][q][0], f1 = sm.flags[y][q][1];
@@ -863,11 +942,11 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
     }
     if (dst) {
       uint4 lab;
-      lab.x = __byte_perm(__byte_perm(l[0], l[1], 0x0040), __byte_perm(l[2], l[3], 0x0040), 0x5410);
-      lab.y = __byte_perm(__byte_perm(l[4], l[5], 0x0040), __byte_perm(l[6], l[7], 0x0040), 0x5410);
-      lab.z = __byte_perm(__byte_perm(l[8], l[9], 0x0040), __byte_perm(l[10], l[11], 0x0040), 0x5410);
-      lab.w = __byte_perm(__byte_perm(l[12], l[13], 0x0040), __byte_perm(l[14], l[15], 0x0040), 0x5410);
-      store_row16(dst, nvalid, lab);
+      lab.x = pack4(l[0], l[1], l[2], l[3], dp);
+      lab.y = pack4(l[4], l[5], l[6], l[7], dp);
+      lab.z = pack4(l[8], l[9], l[10], l[11], dp);
+      lab.w = pack4(l[12], l[13], l[14], l[15], dp);
+      store_labels<STORE>(dst, nvalid, lab);
       dst += lpitch;
     }
   }
@@ -920,24 +999,37 @@ __device__ __forceinline__ void band_vprime(uint8_t* out, int64_t pitch, int64_t
 // chip's counts.  (8-bit images without H/S ranges only: those keep no
 // per-pixel flags.)
 // ---------------------------------------------------------------------------
+// This half-warp's band of chip (cy, cx) of request r (rank's row slice of
+// it when kSplit CTAs share the chip): balanced row bands, one per half-warp.
+template <int DT>
+__device__ __forceinline__ Band chip_band(const Req& r, int chip, int64_t cy, int64_t cx,
+                                          int kSplit, unsigned rank) {
+  const int band = threadIdx.x >> 4;
+  const int64_t y0 = cy * chip, x0 = cx * chip;
+  Band b;
+  b.h = int(min(int64_t(chip), r.H - y0));
+  b.w = int(min(int64_t(chip), r.W - x0));
+  b.pitch = r.pitch;
+  b.chip0 = r.img + x0 * Px<DT>::BPP + y0 * r.pitch;
+  const int s0 = int(rank) * b.h / kSplit, s1 = (int(rank) + 1) * b.h / kSplit;
+  b.r0 = s0 + (band * (s1 - s0)) / n_bands();
+  b.r1 = s0 + ((band + 1) * (s1 - s0)) / n_bands();
+  return b;
+}
+
 template <int DT, bool HS, int kSplit = 1, class SM>
 __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, int chip,
                                            int64_t cy, int64_t cx, SM& sm, uint8_t* lut,
                                            uint8_t* vlut) {
   static_assert(kSplit == 1 || (DT == SIL_U8 && !HS), "split chips: 8-bit, no H/S ranges");
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, band = tid >> 4;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t y0 = cy * chip, x0 = cx * chip;
   const int h = int(min(int64_t(chip), r.H - y0));
   const int w = int(min(int64_t(chip), r.W - x0));
-  int s0 = 0, s1 = h;
   unsigned rank = 0;
-  if (kSplit > 1) {
-    rank = cooperative_groups::this_cluster().block_rank();
-    s0 = int(rank) * h / kSplit;
-    s1 = (int(rank) + 1) * h / kSplit;
-  }
-  // balanced row bands, one per half-warp
-  const int r0 = s0 + (band * (s1 - s0)) / kBands, r1 = s0 + ((band + 1) * (s1 - s0)) / kBands;
+  if (kSplit > 1) rank = cooperative_groups::this_cluster().block_rank();
+  const Band bd = chip_band<DT>(r, chip, cy, cx, kSplit, rank);
+  const int r0 = bd.r0, r1 = bd.r1;
 
   __syncthreads();  // the previous chip of a persistent CTA is done with sm
   if (tid < 256) sm.st.hist[tid] = 0;
@@ -949,14 +1041,14 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
     const bool a4 = ((reinterpret_cast<uintptr_t>(r.img) | uint64_t(r.pitch) | uint64_t(x0)) & 3) == 0;
     if (w == 256) {
       if (a4)
-        band_pass1<DT, HS, true, true>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+        band_pass1<DT, HS, true, true>(bd, dp, sm, n_nodata);
       else
-        band_pass1<DT, HS, true, false>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+        band_pass1<DT, HS, true, false>(bd, dp, sm, n_nodata);
     } else {
       if (a4)
-        band_pass1<DT, HS, false, true>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+        band_pass1<DT, HS, false, true>(bd, dp, sm, n_nodata);
       else
-        band_pass1<DT, HS, false, false>(r.img, r.pitch, y0, x0, h, w, r0, r1, dp, sm, n_nodata);
+        band_pass1<DT, HS, false, false>(bd, dp, sm, n_nodata);
     }
   }
   if (DT == SIL_U16) {
@@ -981,7 +1073,7 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
     uint32_t nd = 0;
     if (DT == SIL_U16) {
 #pragma unroll
-      for (int k = 0; k < kWarps; ++k) nd += sm.st.nod[k];
+      for (int k = 0; k < kMaxWarps; ++k) nd += k < n_warps() ? sm.st.nod[k] : 0u;
     }
     chip_stats_block(sm.st, sm.sc, dp, uint32_t(h * w) - nd);
   }
@@ -1022,7 +1114,19 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
       }
     }
   } else if (r0 < r1 && (HS || r.labels)) {
-    band_pass2<DT, HS>(r.labels, r.lpitch, y0, x0, w, r0, r1, lut, sm, cnt, dp);
+    const uint64_t la = reinterpret_cast<uintptr_t>(r.labels) + uint64_t(x0);
+    const int store = ((la | uint64_t(r.lpitch)) & 15) == 0 ? 16 : ((la | uint64_t(r.lpitch)) & 3) == 0 ? 4 : 1;
+#define SIL_PASS2(S, F) band_pass2<DT, HS, S, F>(r.labels, r.lpitch, y0, x0, w, r0, r1, lut, sm, cnt, dp)
+    if (w == 256) {
+      if (store == 16) SIL_PASS2(16, true);
+      else if (store == 4) SIL_PASS2(4, true);
+      else SIL_PASS2(1, true);
+    } else {
+      if (store == 16) SIL_PASS2(16, false);
+      else if (store == 4) SIL_PASS2(4, false);
+      else SIL_PASS2(1, false);
+    }
+#undef SIL_PASS2
   }
   if (r.vprime && r0 < r1)
     band_vprime<HS || DT == SIL_U16>(r.vprime, r.vpitch, y0, x0, w, r0, r1, vlut, sm);
@@ -1036,7 +1140,7 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
   }
   if (tid < 4) {
     const int c = tid;
-    const int nw = HS ? kWarps : 256 / 32;
+    const int nw = HS ? n_warps() : kBinWarps;
     uint32_t v = 0;
     for (int k = 0; k < nw; ++k) v += sm.st.red[k][c];
     // nodata pixels are left out of the histogram and always masked

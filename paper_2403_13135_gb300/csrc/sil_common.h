@@ -16,9 +16,11 @@ struct DevParams {
   int32_t need_hs;        // 1 if some class range narrows H or S
   uint64_t u16_mul;       // ceil(2^40 / u16_scale): n / s == (n * mul) >> 40
   uint32_t u16_half;      // u16_scale / 2
-  // -1, read from the kernel parameters so that the median's subtractions
-  // stay integer multiply-adds, which issue on a different pipe than min/max.
+  // -1 and 2^8, 2^16, 2^24, read from the kernel parameters so that the
+  // median's subtractions, byte extractions and byte packing stay integer
+  // multiply-adds, which issue on a different pipe than min/max and permutes.
   uint32_t neg1;
+  uint32_t sh8, sh16, sh24;
 };
 
 // One labelling request (a tile or a whole scene) as the kernels see it.
@@ -35,12 +37,19 @@ struct Req {
   int64_t vpitch = 0;
 };
 
-#ifndef SIL_THREADS
-#define SIL_THREADS 320
-#endif
 // Largest chip side handled with the chip resident in shared memory.
 constexpr int kResidentChip = 256;
-constexpr int kThreads = SIL_THREADS;  // 10 warps = 20 half-warp row bands
+// Threads per CTA of the chip kernels: one half-warp row band per 16
+// threads.  256 (16 bands of 16 rows on a 256-row chip) everywhere except
+// where the batch autotuner picks 320 (20 bands of 12-13 rows); shared
+// memory is laid out for the larger.  Each band also decodes the two rows
+// beyond its ends for the median, so fewer, taller bands decode fewer rows
+// twice (16 bands: 12.5 % extra, 20 bands: 15.6 %); 256 was faster than
+// 320 at every request size measured.  At least 256: one thread per
+// histogram bin in the statistics.
+constexpr int kThreadsNarrow = 256;
+constexpr int kThreadsWide = 320;
+constexpr int kMaxThreads = kThreadsWide;
 
 // Validates p and derives DevParams; returns SIL_OK or SIL_EINVAL with a
 // message stored for sil_last_error().

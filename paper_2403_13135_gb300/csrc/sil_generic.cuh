@@ -81,7 +81,7 @@ __device__ void label_chip_generic(const Req& r, const DevParams& dp, int chip,
   if (tid < 256) sm.hist[tid] = 0;
   __syncthreads();
   uint32_t nod = 0;
-  for (int i = tid; i < npx; i += kThreads) {
+  for (int i = tid; i < npx; i += int(blockDim.x)) {
     const int y = i / w, x = i - y * w;
     bool nd = false;
     uint32_t hm;
@@ -96,7 +96,7 @@ __device__ void label_chip_generic(const Req& r, const DevParams& dp, int chip,
   if (lane == 0) sm.nod[tid >> 5] = nod;
   __syncthreads();
   if (tid < 32) {
-    uint32_t nd = (lane < kThreads / 32) ? sm.nod[lane] : 0u;
+    uint32_t nd = (lane < n_warps()) ? sm.nod[lane] : 0u;
     nd = __reduce_add_sync(0xffffffffu, nd);
     chip_stats_warp(sm, dp, uint32_t(npx) - nd);
   }
@@ -104,7 +104,7 @@ __device__ void label_chip_generic(const Req& r, const DevParams& dp, int chip,
   if (tid < 256) lut[tid] = uint8_t(lut_entry<HS>(tid, sm, dp));
   __syncthreads();
   uint32_t cnt[4] = {0, 0, 0, 0};
-  for (int i = tid; i < npx; i += kThreads) {
+  for (int i = tid; i < npx; i += int(blockDim.x)) {
     const int y = i / w, x = i - y * w;
     bool nd;
     uint32_t hm = 0;
@@ -133,7 +133,7 @@ __device__ void label_chip_generic(const Req& r, const DevParams& dp, int chip,
   if (tid < 4) {
     const int c = tid;
     uint32_t v = 0;
-    for (int k = 0; k < kWarps; ++k) v += sm.red[k][c];
+    for (int k = 0; k < n_warps(); ++k) v += sm.red[k][c];
     if (r.chip_counts) r.chip_counts[(cy * r.gx + cx) * 4 + c] = v;
     atomicAdd(&r.counts[c], (unsigned long long)v);
   }

@@ -62,7 +62,9 @@ def test_batch_graph_replay_and_autotune(sil):
     cnts = [torch.empty(4, dtype=torch.int64, device="cuda") for _ in imgs]
     tiles = sil.make_tiles(dev, labs, cnts, None)
     best = sil.autotune(ctx, tiles, len(imgs))
-    assert best >= 1
+    assert best["schedule"] in (sil.SCHED_STRIDE, sil.SCHED_QUEUE, sil.SCHED_PER_CHIP)
+    assert best["threads"] in (256, 320) and best["us"] > 0
+    assert sil.batch_tuning(ctx, tiles, len(imgs)) == (best, True)
     for _ in range(3):  # the same batch replays its cached graph
         sil.label_batch(ctx, tiles, len(imgs))
     torch.cuda.synchronize()
@@ -70,6 +72,39 @@ def test_batch_graph_replay_and_autotune(sil):
         assert np.array_equal(labs[i].cpu().numpy(), a[0][i])
         assert np.array_equal(cnts[i].cpu().numpy(), a[1][i])
     ctx.close()
+
+
+def test_autotune_cache_persists_by_batch_class(sil, tmp_path, monkeypatch):
+    """The tuned schedule is saved under the batch's class and a new context
+    loads it; a batch of another class stays untuned."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SIL_AUTOTUNE_CACHE", str(cache))
+    imgs = _tiles(8, seed=4)
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    labs = [torch.empty(im.shape[:2], dtype=torch.uint8, device="cuda") for im in imgs]
+    cnts = [torch.empty(4, dtype=torch.int64, device="cuda") for _ in imgs]
+    tiles = sil.make_tiles(dev, labs, cnts, None)
+    ctx = sil.Context()
+    assert sil.batch_tuning(ctx, tiles, len(imgs))[1] is False
+    best = sil.autotune(ctx, tiles, len(imgs))
+    ctx.close()
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1
+    key, sched, _ctas, threads, _us = lines[0].split()
+    assert (int(sched), int(threads)) == (best["schedule"], best["threads"])
+    assert key.startswith(torch.cuda.get_device_name(0).replace(" ", "_"))
+    ctx2 = sil.Context()
+    got, tuned = sil.batch_tuning(ctx2, tiles, len(imgs))
+    assert tuned and (got["schedule"], got["threads"]) == (best["schedule"], best["threads"])
+    # one tile of 4096 x 4096: another class (tile and chip counts)
+    big = torch.zeros((4096, 4096, 3), dtype=torch.uint8, device="cuda")
+    cb = torch.empty(4, dtype=torch.int64, device="cuda")
+    t2 = sil.make_tiles([big], None, [cb], None)
+    assert sil.batch_tuning(ctx2, t2, 1)[1] is False
+    sil.label_batch(ctx2, t2, 1)
+    torch.cuda.synchronize()
+    assert int(cb[2]) == 4096 * 4096  # black: all open water
+    ctx2.close()
 
 
 def test_batch_other_variants(sil):
