@@ -755,7 +755,7 @@ def main():
     ap.add_argument("--config", default="scene", choices=["scene", "batch", "served", "sweep", "unet"],
                     help="scene: the headline line; batch/served/sweep/unet: the other workloads")
     ap.add_argument("--unet-width", type=int, default=32)
-    ap.add_argument("--unet-depth", type=int, default=4)
+    ap.add_argument("--unet-depth", type=int, default=5)
     ap.add_argument("--unet-batch", type=int, default=64)
     ap.add_argument("--unet-steps", type=int, default=50)
     ap.add_argument("--tiles", type=int, default=512)

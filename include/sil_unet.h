@@ -47,7 +47,8 @@ typedef struct sil_unet sil_unet;
 
 typedef struct sil_unet_config {
   int32_t base_width; /* F: 16, 32 or 64 (default 32) */
-  int32_t depth;      /* encoder levels: 1..4 (default 4) */
+  int32_t depth;      /* encoder levels: 1..5 (default 5: the paper's 28
+                         convolution layers, Sec. III-C "U-Net Training") */
   int32_t max_batch;  /* chips per sil_unet_forward call: 1..4096 (default 32) */
 } sil_unet_config;
 
@@ -58,11 +59,13 @@ typedef enum sil_unet_layer_kind {
   SIL_UNET_HEAD = 2   /* 1x1 conv to 3 scores, weight [3][F][1][1] */
 } sil_unet_layer_kind;
 
-/* Fills F = 32, depth = 4, max_batch = 32.  SIL_EINVAL on NULL. */
+/* Fills F = 32, depth = 5, max_batch = 32.  SIL_EINVAL on NULL. */
 sil_status sil_unet_config_default(sil_unet_config* cfg);
 
-/* Number of weighted layers: 4 depth + 4 (2 per encoder level, 2 at the
- * bottom, 3 per decoder level, 1 head); -1 if depth is out of range. */
+/* Number of weighted layers: 5 depth + 3 (2 per encoder level, 2 at the
+ * bottom, 3 per decoder level, 1 head; 28 at depth 5, the paper's count of
+ * five downsampling steps, a bottleneck and five upsampling steps); -1 if
+ * depth is out of range. */
 int32_t sil_unet_num_layers(int32_t depth);
 
 /* Shape of layer i in this order: enc0_0, enc0_1, enc1_0, ..., bott_0,

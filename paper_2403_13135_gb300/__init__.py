@@ -453,7 +453,7 @@ class sil_unet_config(ctypes.Structure):
 UNET_CONV3, UNET_UP, UNET_HEAD = 0, 1, 2
 
 
-def unet_config(base_width: int = 32, depth: int = 4, max_batch: int = 32) -> sil_unet_config:
+def unet_config(base_width: int = 32, depth: int = 5, max_batch: int = 32) -> sil_unet_config:
     c = sil_unet_config()
     check(_lib.sil_unet_config_default(ctypes.byref(c)))
     c.base_width, c.depth, c.max_batch = int(base_width), int(depth), int(max_batch)
@@ -463,7 +463,10 @@ def unet_config(base_width: int = 32, depth: int = 4, max_batch: int = 32) -> si
 def unet_layer_shapes(cfg: sil_unet_config):
     """[(weight shape, kind)] in the library's layer order."""
     out = []
-    for i in range(_lib.sil_unet_num_layers(cfg.depth)):
+    nl = _lib.sil_unet_num_layers(cfg.depth)
+    if nl < 0:
+        raise SilError(SIL_EINVAL, f"U-Net depth {cfg.depth} out of range")
+    for i in range(nl):
         dims = (_I64 * 4)()
         kind = _I32()
         check(_lib.sil_unet_layer_shape(ctypes.byref(cfg), i, dims, ctypes.byref(kind)))

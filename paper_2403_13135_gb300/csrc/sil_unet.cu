@@ -46,7 +46,7 @@ constexpr int kEpilogue = 128;     // warps 4-7: accumulator -> bf16 output
 constexpr int kConvThreads = 288;  // + warp 8: MMA issue
 constexpr int kInCh = 8;           // prepared input channels (R, G, B, 5 zeros)
 constexpr int kClasses = 3;
-constexpr int kMaxCout = 1024;     // widest layer: F = 64 at depth 4
+constexpr int kMaxCout = 2048;     // widest layer: F = 64 at depth 5
 
 struct ConvArgs {
   const __nv_bfloat16* x;  // input, first channel of pixel 0
@@ -73,18 +73,40 @@ struct ConvArgs {
                            // 2 two 32-channel boxes (two taps) per stage (Ci = 32)
   int fault_it;            // test hook: stage whose A box is never issued (-1: none)
   unsigned int* err;       // count of bounded waits that ran out
+  int tw;                  // tile width: 16 (8 rows x 16 pixels of one image) or
+                           // 8 (the 8 x 8 pixels of two images; H = W = 8)
 };
 
-// A tile is 8 image rows x 16 pixels of one image: tile row r is pixel
-// (y0 + r / 16, x0 + r % 16).  A 2x2 pooling window is then lanes l, l ^ 1,
-// l ^ 16, l ^ 17 of one epilogue warp.
+// A tile is 128 pixels.  Width 16: 8 image rows x 16 pixels of one image,
+// tile row r is pixel (y0 + r / 16, x0 + r % 16), and a 2x2 pooling window
+// is lanes l, l ^ 1, l ^ 16, l ^ 17 of one epilogue warp.  Width 8 (the
+// 8 x 8 maps of the fifth level): the whole 8 x 8 images 2 mt and 2 mt + 1,
+// tile row r is pixel (r % 64 / 8, r % 8) of image 2 mt + r / 64.
 constexpr int kTileW = 16, kTileH = 8;
-__device__ __forceinline__ void tile_origin(int mt, int H, int W, int& b, int& y0, int& x0) {
+__device__ __forceinline__ void tile_origin(int mt, int H, int W, int tw, int& b, int& y0, int& x0) {
+  if (tw == 8) {
+    b = 2 * mt;
+    y0 = x0 = 0;
+    return;
+  }
   const int tx = W / kTileW, per_img = (H / kTileH) * tx;
   b = mt / per_img;
   const int rem = mt - b * per_img, ty = rem / tx;
   y0 = ty * kTileH;
   x0 = (rem - ty * tx) * kTileW;
+}
+// Image and pixel of tile row r.
+__device__ __forceinline__ void tile_pixel(int r, int tw, int b0, int y0, int x0, int& b, int& y,
+                                           int& x) {
+  if (tw == 8) {
+    b = b0 + (r >> 6);
+    y = (r >> 3) & 7;
+    x = r & 7;
+  } else {
+    b = b0;
+    y = y0 + (r >> 4);
+    x = x0 + (r & 15);
+  }
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -223,7 +245,7 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
       for (int t = blockIdx.x; t < ntotal && ok; t += gridDim.x) {
         const int mt = t / ntiles, nt = t - mt * ntiles;
         int b, y0, x0;
-        tile_origin(mt, a.H, a.W, b, y0, x0);
+        tile_origin(mt, a.H, a.W, a.tw, b, y0, x0);
         for (int kt = 0; kt < a.KT; ++kt, ++it) {
           const int s = it % S;
           if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), uint32_t((it / S - 1) & 1), failed)) {
@@ -293,12 +315,13 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
       // (bit 0 above, 1 below, 2 left, 3 right, 4 the pixel itself)
       int64_t pbase[8];
       uint32_t pfl[8];
-      int b, y0, x0;
-      tile_origin(mt, a.H, a.W, b, y0, x0);
+      int b0, y0, x0;
+      tile_origin(mt, a.H, a.W, a.tw, b0, y0, x0);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int r = 32 * warp + 4 * i + (lane >> 3);
-        const int y = y0 + (r >> 4), x = x0 + (r & 15);
+        int b, y, x;
+        tile_pixel(r, a.tw, b0, y0, x0, b, y, x);
         pbase[i] = ((int64_t(b) * a.H + y) * a.W + x) * a.xs;
         pfl[i] = mt * kBM + r < a.M ? (16u | (y > 0 ? 1u : 0u) | (y < a.H - 1 ? 2u : 0u) |
                                        (x > 0 ? 4u : 0u) | (x < a.W - 1 ? 8u : 0u))
@@ -371,9 +394,9 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int p = mt * kBM + r;
-      int b, y0, x0;
-      tile_origin(mt, a.H, a.W, b, y0, x0);
-      const int y = y0 + (r >> 4), x = x0 + (r & 15);
+      int b0, y0, x0, b, y, x;
+      tile_origin(mt, a.H, a.W, a.tw, b0, y0, x0);
+      tile_pixel(r, a.tw, b0, y0, x0, b, y, x);
       const bool live = p < a.M;
       float hacc[kClasses];
 #pragma unroll
@@ -604,6 +627,7 @@ struct Layer {
   __nv_bfloat16* pool = nullptr;  // fused 2x2 max pool output (encoder second convs)
   bool head = false;              // fused 1x1 head (last decoder conv)
   int tma = 0;                    // A tiles through a tensor map (see ConvArgs::tma)
+  int tw = kTileW;                // tile width (see ConvArgs::tw)
   CUtensorMap tmap{};             // 4-D map of the input: {Ci, W, H, max_batch}
 };
 
@@ -634,7 +658,7 @@ using namespace sil::unet;
 
 bool config_ok(const sil_unet_config* c) {
   return c && (c->base_width == 16 || c->base_width == 32 || c->base_width == 64) &&
-         c->depth >= 1 && c->depth <= 4 && c->max_batch >= 1 && c->max_batch <= 4096;
+         c->depth >= 1 && c->depth <= 5 && c->max_batch >= 1 && c->max_batch <= 4096;
 }
 
 int ilog2(int v) {
@@ -688,8 +712,9 @@ bool encode_input_map(Layer& L, int batch) {
   const cuuint64_t es = 2;
   const cuuint64_t strides[3] = {cuuint64_t(L.in.stride) * es, cuuint64_t(L.in.W) * L.in.stride * es,
                                  cuuint64_t(L.in.H) * L.in.W * L.in.stride * es};
-  const cuuint32_t box[4] = {cuuint32_t(L.tma == 2 ? kBK / 2 : kBK), cuuint32_t(kTileW),
-                             cuuint32_t(kTileH), 1};
+  // a tile of width 16: 16 x 8 pixels of one image; of width 8: two 8 x 8 images
+  const cuuint32_t box[4] = {cuuint32_t(L.tma == 2 ? kBK / 2 : kBK), cuuint32_t(L.tw),
+                             cuuint32_t(kTileH), cuuint32_t(L.tw == 8 ? 2 : 1)};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return enc(&L.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, L.in.base, dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -760,6 +785,7 @@ cudaError_t run_layer(const Layer& L, int n, unsigned int* err, const float* hea
   a.tma = L.tma;
   a.fault_it = (fault && L.tma) ? 0 : -1;
   a.err = err;
+  a.tw = L.tw;
   const int mtiles = (a.M + kBM - 1) / kBM, ntiles = L.N / L.NT;
   switch (L.NT) {
     case 16: return launch_conv_nt<16>(a, L.tmap, mtiles, ntiles, s);
@@ -810,13 +836,13 @@ extern "C" sil_status sil_unet_config_default(sil_unet_config* cfg) {
     return SIL_EINVAL;
   }
   cfg->base_width = 32;
-  cfg->depth = 4;
+  cfg->depth = 5;
   cfg->max_batch = 32;
   return SIL_OK;
 }
 
 extern "C" int32_t sil_unet_num_layers(int32_t depth) {
-  return (depth >= 1 && depth <= 4) ? 5 * depth + 3 : -1;
+  return (depth >= 1 && depth <= 5) ? 5 * depth + 3 : -1;
 }
 
 extern "C" sil_status sil_unet_layer_shape(const sil_unet_config* cfg, int32_t i, int64_t dims[4],
@@ -875,7 +901,7 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
                                       const float* const* weights, const float* const* biases,
                                       int32_t device) {
   if (!out || !config_ok(cfg) || !weights || !biases) {
-    set_error("sil_unet_create: NULL argument or config outside F in {16,32,64}, depth 1..4, "
+    set_error("sil_unet_create: NULL argument or config outside F in {16,32,64}, depth 1..5, "
               "max_batch 1..4096");
     return SIL_EINVAL;
   }
@@ -1016,6 +1042,9 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
         L.head = l == 0;
       }
     }
+    // the fifth level's 8 x 8 maps are tiled two images at a time
+    L.tw = L.in.W >= kTileW ? kTileW : 8;
+    if (L.tw == 8 && (L.in.W != 8 || L.in.H != 8 || L.pool || L.head)) st = SIL_EINVAL;
     // inputs whose channel count is a multiple of 64 are read by tensor map
     if (L.tma && !encode_input_map(L, B)) L.tma = 0;
     // weights -> swizzled bf16 blocks [N / NT][KT][NT x 64]
