@@ -91,7 +91,7 @@ def test_unet_host_calls_without_gpu(sil):
     """Layer shapes and flop count agree with the seeded generator's layer
     table; bad configs are rejected on the host."""
     import synth
-    for F, depth in ((16, 1), (32, 4), (64, 3)):
+    for F, depth in ((16, 1), (32, 4), (64, 3), (32, 5), (64, 5)):
         cfg = sil.unet_config(F, depth, 4)
         got = sil.unet_layer_shapes(cfg)
         ref = synth.unet_layer_shapes(F, depth)
@@ -117,6 +117,7 @@ def test_unet_host_calls_without_gpu(sil):
     dims = (ctypes.c_int64 * 4)()
     kind = ctypes.c_int32()
     assert sil._lib.sil_unet_layer_shape(ctypes.byref(bad), 0, dims, ctypes.byref(kind)) == sil.SIL_EINVAL
-    assert sil._lib.sil_unet_num_layers(5) == -1
+    assert sil._lib.sil_unet_num_layers(5) == 28
+    assert sil._lib.sil_unet_num_layers(6) == -1 and sil._lib.sil_unet_num_layers(0) == -1
     h = ctypes.c_void_p()
     assert sil._lib.sil_unet_create(ctypes.byref(h), ctypes.byref(bad), None, None, 0) == sil.SIL_EINVAL
