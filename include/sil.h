@@ -325,6 +325,49 @@ sil_status sil_render(const uint8_t* labels, int64_t label_pitch, int64_t H,
                       int64_t W, uint8_t* rgb, int64_t rgb_pitch,
                       sil_stream stream);
 
+/* ---------------------------------------------------------------------
+ * Evaluation metrics (Sec. IV-A "Evaluation Metrics"): accuracy,
+ * precision, recall, F1 score, and the confusion matrix whose element in
+ * row A, column B is the number of pixels predicted as A over the number of
+ * pixels of reference class B (each column adds up to 1).  Computed on the
+ * host from the counts of sil_confusion.  Over the paper's three classes:
+ * pixels whose reference is masked (code 3) are left out; a prediction of
+ * masked counts as a miss of the pixel's reference class (row 3 of the
+ * matrix).  A ratio whose denominator is zero is 0.  The paper reports one
+ * precision / recall / F1 figure per model; macro_* are the unweighted
+ * means over the three classes, weighted_* the means weighted by each
+ * class's reference pixel count.
+ * ------------------------------------------------------------------- */
+typedef struct sil_metrics {
+  double accuracy;
+  double precision[3], recall[3], f1[3];  /* thick, thin, water */
+  double macro_precision, macro_recall, macro_f1;
+  double weighted_precision, weighted_recall, weighted_f1;
+  double matrix[4][4];  /* [pred][ref]; columns 0..2 sum to 1, column 3 is 0 */
+  uint64_t support[3];  /* reference pixels of each class */
+} sil_metrics;
+
+/* conf: HOST uint64[4][4] indexed [pred][ref] (as sil_confusion writes it,
+ * copied to the host).  SIL_EINVAL on NULL. */
+sil_status sil_metrics_from_confusion(const uint64_t* conf, sil_metrics* out);
+
+/* The paper's training pairs (Sec. III-A colour masks; Sec. III-C cuts
+ * scenes into 256 x 256 images): chips k0 .. k0 + n - 1 of the chip grid
+ * of side `chip` anchored at (0, 0), row-major over the grid, each as the
+ * image chip and its colour-mask chip (red thick ice, blue thin ice, green
+ * open water, black masked), zero past the scene's right and bottom edges.
+ *   img      DEVICE uint8 H x W x 3, pitch_bytes per row (>= 3 W)
+ *   labels   DEVICE uint8 H x W codes 0..3, label_pitch per row (>= W)
+ *   chips    DEVICE uint8 [n][chip][chip][3] or NULL
+ *   masks    DEVICE uint8 [n][chip][chip][3] or NULL
+ * chip 4..512; 0 <= k0, k0 + n <= the grid's chip count, n >= 1.
+ * Asynchronous on `stream`. */
+sil_status sil_export_chips(const uint8_t* img, int64_t H, int64_t W,
+                            int64_t pitch_bytes, const uint8_t* labels,
+                            int64_t label_pitch, int32_t chip, int64_t k0,
+                            int64_t n, uint8_t* chips, uint8_t* masks,
+                            sil_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

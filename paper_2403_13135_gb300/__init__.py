@@ -68,6 +68,15 @@ class sil_tuning(ctypes.Structure):
 SCHED_STRIDE, SCHED_QUEUE, SCHED_PER_CHIP = 0, 1, 2
 
 
+class sil_metrics(ctypes.Structure):
+    _fields_ = [("accuracy", ctypes.c_double), ("precision", ctypes.c_double * 3),
+                ("recall", ctypes.c_double * 3), ("f1", ctypes.c_double * 3),
+                ("macro_precision", ctypes.c_double), ("macro_recall", ctypes.c_double),
+                ("macro_f1", ctypes.c_double), ("weighted_precision", ctypes.c_double),
+                ("weighted_recall", ctypes.c_double), ("weighted_f1", ctypes.c_double),
+                ("matrix", (ctypes.c_double * 4) * 4), ("support", ctypes.c_uint64 * 3)]
+
+
 class sil_server_config(ctypes.Structure):
     _fields_ = [
         ("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
@@ -118,6 +127,8 @@ _SIGS = {
     "sil_server_destroy": ([_P], None),
     "sil_confusion": ([_P, _I64, _P, _I64, _I64, _I64, _I32, _P, _P, _P], _I32),
     "sil_render": ([_P, _I64, _I64, _I64, _P, _I64, _P], _I32),
+    "sil_metrics_from_confusion": ([_P, ctypes.POINTER(sil_metrics)], _I32),
+    "sil_export_chips": ([_P, _I64, _I64, _I64, _P, _I64, _I32, _I64, _I64, _P, _P, _P], _I32),
     "sil_unet_config_default": ([ctypes.c_void_p], _I32),
     "sil_unet_num_layers": ([_I32], _I32),
     "sil_unet_layer_shape": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I32)], _I32),
@@ -363,6 +374,38 @@ def render(labels, stream=None):
     check(_lib.sil_render(labels.data_ptr(), labels.stride(0), H, W, rgb.data_ptr(), 3 * W,
                           _stream_handle(stream)))
     return rgb
+
+
+def metrics(conf) -> dict:
+    """Sec. IV-A metrics of a 4 x 4 confusion count matrix [pred][ref]
+    (host numpy or a torch tensor; sil_metrics_from_confusion)."""
+    c = np.ascontiguousarray(np.asarray(conf.cpu() if hasattr(conf, "cpu") else conf,
+                                        dtype=np.uint64).reshape(16))
+    m = sil_metrics()
+    check(_lib.sil_metrics_from_confusion(c.ctypes.data, ctypes.byref(m)))
+    return {"accuracy": m.accuracy, "precision": list(m.precision), "recall": list(m.recall),
+            "f1": list(m.f1), "macro_precision": m.macro_precision, "macro_recall": m.macro_recall,
+            "macro_f1": m.macro_f1, "weighted_precision": m.weighted_precision,
+            "weighted_recall": m.weighted_recall, "weighted_f1": m.weighted_f1,
+            "matrix": [list(r) for r in m.matrix], "support": [int(v) for v in m.support]}
+
+
+def export_chips(img, labels, chip: int = 256, k0: int = 0, n: int | None = None, stream=None):
+    """Image chips and colour-mask chips of a device scene and its labels
+    (sil_export_chips): chips k0 .. k0 + n - 1 of the chip grid, each
+    [chip, chip, 3] uint8; returns (chips, masks) device tensors [n, ...]."""
+    import torch
+    H, W, pitch, dt = _img_geometry(img)
+    assert dt == SIL_U8, "uint8 images"
+    gy, gx = -(-H // chip), -(-W // chip)
+    if n is None:
+        n = gy * gx - k0
+    chips = torch.empty((n, chip, chip, 3), dtype=torch.uint8, device=img.device)
+    masks = torch.empty((n, chip, chip, 3), dtype=torch.uint8, device=img.device)
+    check(_lib.sil_export_chips(img.data_ptr(), H, W, pitch, labels.data_ptr(), labels.stride(0),
+                                int(chip), int(k0), int(n), chips.data_ptr(), masks.data_ptr(),
+                                _stream_handle(stream)))
+    return chips, masks
 
 
 class Server:

@@ -331,6 +331,61 @@ __global__ void k_render(const uint8_t* labels, int64_t lp, int64_t H, int64_t W
   }
 }
 
+// Chips k0 .. k0 + n - 1 of the chip grid as image chips and colour-mask
+// chips (thick ice red, thin ice blue, open water green, masked black; zero
+// past the scene's edges).  A thread handles 4 consecutive pixels of one
+// chip row: 12 image bytes and 4 labels in, 12 + 12 bytes out as words.
+__global__ void k_export(const uint8_t* img, int64_t H, int64_t W, int64_t pitch,
+                         const uint8_t* labels, int64_t lp, int chip, int gx, int64_t k0,
+                         int64_t n, uint8_t* chips, uint8_t* masks) {
+  const uint32_t pal[4] = {0x0000FFu, 0xFF0000u, 0x00FF00u, 0x000000u};
+  const int q = chip >> 2;  // groups of 4 pixels per chip row (chip % 4 handled below)
+  const int qr = (chip + 3) >> 2;
+  const int64_t groups = n * chip * qr;
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < groups;
+       g += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t c = g / (int64_t(chip) * qr);
+    const int rem = int(g - c * chip * qr), yy = rem / qr, x4 = 4 * (rem - (rem / qr) * qr);
+    const int64_t k = k0 + c;
+    const int64_t sy = (k / gx) * chip + yy, sx0 = (k % gx) * chip + x4;
+    uint8_t px[12], mk[12];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t sx = sx0 + j;
+      const bool in = sy < H && sx < W && x4 + j < chip;
+      const uint8_t* s = img + sy * pitch + 3 * sx;
+      const uint32_t col = in ? pal[labels[sy * lp + sx] & 3u] : 0u;
+      px[3 * j] = in ? s[0] : 0;
+      px[3 * j + 1] = in ? s[1] : 0;
+      px[3 * j + 2] = in ? s[2] : 0;
+      mk[3 * j] = uint8_t(col);
+      mk[3 * j + 1] = uint8_t(col >> 8);
+      mk[3 * j + 2] = uint8_t(col >> 16);
+    }
+    const int64_t o = ((c * chip + yy) * chip + x4) * 3;
+    const int nb = 3 * min(4, chip - x4);
+    if (nb == 12 && ((o & 3) == 0)) {
+      uint32_t a[3], b[3];
+      memcpy(a, px, 12);
+      memcpy(b, mk, 12);
+      if (chips) {
+        uint32_t* d = reinterpret_cast<uint32_t*>(chips + o);
+        d[0] = a[0]; d[1] = a[1]; d[2] = a[2];
+      }
+      if (masks) {
+        uint32_t* d = reinterpret_cast<uint32_t*>(masks + o);
+        d[0] = b[0]; d[1] = b[1]; d[2] = b[2];
+      }
+    } else {
+      for (int j = 0; j < nb; ++j) {
+        if (chips) chips[o + j] = px[j];
+        if (masks) masks[o + j] = mk[j];
+      }
+    }
+  }
+  (void)q;
+}
+
 }  // namespace sil
 
 using namespace sil;
@@ -663,6 +718,70 @@ sil_status sil_render(const uint8_t* labels, int64_t label_pitch, int64_t H, int
   k_render<<<int(want < cap ? want : cap), 256, 0, s>>>(labels, label_pitch, H, W, rgb, rgb_pitch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sil_render: launch");
+  return SIL_OK;
+}
+
+sil_status sil_metrics_from_confusion(const uint64_t* conf, sil_metrics* out) {
+  g_err[0] = 0;
+  if (!conf || !out) {
+    set_error("sil_metrics_from_confusion: NULL argument");
+    return SIL_EINVAL;
+  }
+  memset(out, 0, sizeof(*out));
+  auto div = [](double a, double b) { return b != 0.0 ? a / b : 0.0; };
+  double col[3] = {0, 0, 0}, row[4] = {0, 0, 0, 0}, total = 0, tp = 0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 3; ++b) {  // the reference-masked column is left out
+      const double v = double(conf[a * 4 + b]);
+      col[b] += v;
+      row[a] += v;
+      total += v;
+    }
+  for (int k = 0; k < 3; ++k) {
+    const double t = double(conf[k * 4 + k]);
+    tp += t;
+    out->precision[k] = div(t, row[k]);
+    out->recall[k] = div(t, col[k]);
+    out->f1[k] = div(2.0 * out->precision[k] * out->recall[k], out->precision[k] + out->recall[k]);
+    out->support[k] = conf[0 * 4 + k] + conf[1 * 4 + k] + conf[2 * 4 + k] + conf[3 * 4 + k];
+    const double w = div(col[k], total);
+    out->macro_precision += out->precision[k] / 3.0;
+    out->macro_recall += out->recall[k] / 3.0;
+    out->macro_f1 += out->f1[k] / 3.0;
+    out->weighted_precision += out->precision[k] * w;
+    out->weighted_recall += out->recall[k] * w;
+    out->weighted_f1 += out->f1[k] * w;
+  }
+  out->accuracy = div(tp, total);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 3; ++b) out->matrix[a][b] = div(double(conf[a * 4 + b]), col[b]);
+  return SIL_OK;
+}
+
+sil_status sil_export_chips(const uint8_t* img, int64_t H, int64_t W, int64_t pitch_bytes,
+                            const uint8_t* labels, int64_t label_pitch, int32_t chip, int64_t k0,
+                            int64_t n, uint8_t* chips, uint8_t* masks, sil_stream stream) {
+  g_err[0] = 0;
+  if (!img || !labels || H < 1 || W < 1 || pitch_bytes < 3 * W || label_pitch < W || chip < 4 ||
+      chip > 512) {
+    set_error("sil_export_chips: invalid arguments");
+    return SIL_EINVAL;
+  }
+  const int64_t gx = (W + chip - 1) / chip, gy = (H + chip - 1) / chip;
+  if (k0 < 0 || n < 1 || k0 + n > gx * gy) {
+    set_error("sil_export_chips: chips %lld..%lld outside the grid of %lld", (long long)k0,
+              (long long)(k0 + n - 1), (long long)(gx * gy));
+    return SIL_EINVAL;
+  }
+  if (!chips && !masks) return SIL_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t groups = n * chip * ((chip + 3) / 4);
+  const int64_t cap = int64_t(device_sm_count()) * 8;
+  const int64_t want = (groups + 255) / 256;
+  k_export<<<int(want < cap ? want : cap), 256, 0, s>>>(img, H, W, pitch_bytes, labels, label_pitch,
+                                                        chip, int(gx), k0, n, chips, masks);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sil_export_chips: launch");
   return SIL_OK;
 }
 
