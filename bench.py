@@ -501,10 +501,10 @@ def run_served(args):
         lab_scenes.put(torch.empty((SIDE, SIDE), dtype=torch.uint8).pin_memory().numpy())
     results = []
     for rate in [float(r) for r in args.rates.split(",")]:
-        lat, px = [], [0]
+        lat, svc, px = [], [], [0]
         stalls = 0
         pending = queue.Queue()
-        with sil.Server(max_inflight=128, max_batch=32, want_labels=True) as srv:
+        with sil.Server(max_inflight=128, want_labels=True) as srv:
             def collector():
                 while True:
                     item = pending.get()
@@ -513,6 +513,7 @@ def run_served(args):
                     rid, n, buf, q = item
                     r = srv.wait(rid, 600000)
                     lat.append(r["t_done_ms"] - r["t_submit_ms"])
+                    svc.append(r["t_done_ms"] - r["t_admit_ms"])
                     px[0] += n
                     q.put(buf)
             th = threading.Thread(target=collector, daemon=True)
@@ -543,11 +544,14 @@ def run_served(args):
             pending.put(None)
             th.join()
             t_all = time.perf_counter() - t0
+            stats = srv.stats()
         lat = np.array(lat)
         results.append({"rate_req_s": rate, "requests": int(len(lat)), "seconds": t_all,
                         "throughput_gpx_s": px[0] / t_all / 1e9, "req_s": len(lat) / t_all,
                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                        "backpressure_waits": stalls})
+                        "service_p50_ms": float(np.percentile(svc, 50)),
+                        "service_p99_ms": float(np.percentile(svc, 99)),
+                        "backpressure_waits": stalls, "kernel_launches": stats["kernel_launches"]})
         print(json.dumps({"served": results[-1]}), flush=True)
     print(json.dumps({"metric": "served labelling: throughput and p50/p99 latency",
                       "config": {"workload": "Poisson arrivals; 90% square tiles side U{256..4096}, "
@@ -760,7 +764,7 @@ def main():
     ap.add_argument("--unet-steps", type=int, default=50)
     ap.add_argument("--tiles", type=int, default=512)
     ap.add_argument("--rates", default="50,200,1000,2000")
-    ap.add_argument("--served-seconds", type=float, default=10.0)
+    ap.add_argument("--served-seconds", type=float, default=60.0)
     ap.add_argument("--label-pool", type=int, default=96)
     ap.add_argument("--scenes", type=int, default=32)
     ap.add_argument("--distinct", type=int, default=4)

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define SIL_ABI_VERSION 1
+#define SIL_ABI_VERSION 2
 
 /* cudaStream_t is `struct CUstream_st*`; declared here so this header does
  * not need the CUDA headers. */
@@ -260,9 +260,21 @@ sil_status sil_batch_tuning(const sil_tile* tiles, int32_t n, sil_dtype dt,
 /* ---------------------------------------------------------------------
  * Served labeling: a continuous-batching request loop.  Requests arrive at
  * any time with HOST images (pinned memory recommended); they are admitted
- * when device memory and a slot are free, copied in on an ingest stream,
- * labelled by persistent launches that take every admitted request at once,
- * and completed with results copied back to the caller's host buffers.
+ * in arrival order when device memory and a request slot are free, and
+ * copied in on an ingest stream.  After its image copy, each request is
+ * published to a device-resident request ring: its descriptor, its "ready"
+ * word and the ring's count of published chips are written by copies that
+ * follow the image copy on the same stream.  A persistent kernel (one CTA
+ * per resident slot) claims published chips one at a time, in publication
+ * order, with an atomic compare-and-swap on the ring's claim counter, so
+ * requests that arrive while others run are taken up by the running kernel
+ * without a new launch; the CTA that finishes a request's last chip marks
+ * the request complete in host-mapped memory, and its results are copied
+ * back on an egress stream.  Every device wait is bounded: a CTA with no
+ * published chip for idle_timeout_us exits (the host relaunches the kernel
+ * when work arrives), and a chip whose request's ready word has not arrived
+ * within ready_timeout_ms is skipped and its request ends with
+ * SIL_ETIMEOUT.
  * ------------------------------------------------------------------- */
 typedef struct sil_server sil_server;
 
@@ -271,8 +283,13 @@ typedef struct sil_server_config {
   int32_t max_inflight;       /* request slots (default 64) */
   int64_t device_mem_budget;  /* bytes of device memory for request buffers;
                                  0 = 50% of free memory at create */
-  int32_t max_batch;          /* requests per launch (default 32) */
+  int32_t max_batch;          /* unused (the ring kernel takes requests one
+                                 chip at a time); kept for compatibility */
   int32_t want_labels;        /* 1: copy labels back (default 1) */
+  int32_t ready_timeout_ms;   /* device wait for a published request's
+                                 image (default 2000) */
+  int32_t idle_timeout_us;    /* a kernel CTA with no work exits after this
+                                 (default 5000) */
 } sil_server_config;
 
 typedef struct sil_request_result {
@@ -294,14 +311,32 @@ sil_status sil_server_submit(sil_server* srv, const void* img, int64_t H,
                              int64_t label_pitch, uint32_t* chip_counts,
                              int64_t* id);
 /* Wait up to timeout_ms (-1 = no limit) for request `id` to complete.
- * SIL_ETIMEOUT if it did not complete in time. */
+ * SIL_OK once it has completed, whatever its outcome: out->status is the
+ * request's own status (SIL_OK; SIL_ETIMEOUT when the device's wait for its
+ * image ran out; SIL_ECANCELED; SIL_ECUDA), and the request is released.
+ * SIL_ETIMEOUT if it did not complete within timeout_ms (it stays
+ * queryable); SIL_EINVAL for an unknown id. */
 sil_status sil_server_wait(sil_server* srv, int64_t id, int64_t timeout_ms,
                            sil_request_result* out);
-/* Non-blocking: SIL_OK and *out filled if done, SIL_EBUSY if not yet. */
+/* Non-blocking: SIL_OK and *out filled (out->status = the request's
+ * status) if done, SIL_EBUSY if not yet, SIL_EINVAL for an unknown id. */
 sil_status sil_server_poll(sil_server* srv, int64_t id, sil_request_result* out);
 /* Cancel a request that has not been admitted yet (SIL_EBUSY if it is
  * already running). */
 sil_status sil_server_cancel(sil_server* srv, int64_t id);
+/* Persistent-kernel launches since the server was created and chips
+ * published to its ring (either pointer may be NULL).  Requests that arrive
+ * while the kernel runs are taken up without a launch. */
+sil_status sil_server_stats(sil_server* srv, int64_t* kernel_launches,
+                            int64_t* chips_published);
+
+/* Test hook for the bounded device waits (no GPU fault): while set, the
+ * next request to be published gets its descriptor and chips published but
+ * never its ready word, so every chip of it waits ready_timeout_ms and the
+ * request completes with SIL_ETIMEOUT; later requests are unaffected.
+ * skip_ready = 0 clears the hook. */
+sil_status sil_server_set_fault(sil_server* srv, int32_t skip_ready);
+
 /* Stop accepting work, cancel pending requests, wait for running ones and
  * free everything. */
 void sil_server_destroy(sil_server* srv);

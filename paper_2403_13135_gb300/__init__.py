@@ -81,7 +81,8 @@ class sil_server_config(ctypes.Structure):
     _fields_ = [
         ("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
         ("device_mem_budget", ctypes.c_int64), ("max_batch", ctypes.c_int32),
-        ("want_labels", ctypes.c_int32),
+        ("want_labels", ctypes.c_int32), ("ready_timeout_ms", ctypes.c_int32),
+        ("idle_timeout_us", ctypes.c_int32),
     ]
 
 
@@ -125,6 +126,8 @@ _SIGS = {
     "sil_server_poll": ([_P, _I64, ctypes.POINTER(sil_request_result)], _I32),
     "sil_server_cancel": ([_P, _I64], _I32),
     "sil_server_destroy": ([_P], None),
+    "sil_server_stats": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], _I32),
+    "sil_server_set_fault": ([_P, _I32], _I32),
     "sil_confusion": ([_P, _I64, _P, _I64, _I64, _I64, _I32, _P, _P, _P], _I32),
     "sil_render": ([_P, _I64, _I64, _I64, _P, _I64, _P], _I32),
     "sil_metrics_from_confusion": ([_P, ctypes.POINTER(sil_metrics)], _I32),
@@ -414,9 +417,14 @@ class Server:
     copies) kept alive here until their request completes."""
 
     def __init__(self, dt: int = SIL_U8, p=None, *, device: int = 0, max_inflight: int = 64,
-                 mem_budget: int = 0, max_batch: int = 32, want_labels: bool = True):
+                 mem_budget: int = 0, max_batch: int = 32, want_labels: bool = True,
+                 ready_timeout_ms: int | None = None, idle_timeout_us: int | None = None):
         cfg = sil_server_config()
         check(_lib.sil_server_config_default(ctypes.byref(cfg)))
+        if ready_timeout_ms is not None:
+            cfg.ready_timeout_ms = int(ready_timeout_ms)
+        if idle_timeout_us is not None:
+            cfg.idle_timeout_us = int(idle_timeout_us)
         cfg.device, cfg.max_inflight, cfg.device_mem_budget = device, max_inflight, mem_budget
         cfg.max_batch, cfg.want_labels = max_batch, int(want_labels)
         self.dt = dt
@@ -444,27 +452,41 @@ class Server:
                 "t_submit_ms": r.t_submit_ms, "t_admit_ms": r.t_admit_ms, "t_done_ms": r.t_done_ms}
 
     def wait(self, rid: int, timeout_ms: int = -1) -> dict:
+        """Result of request rid once it has completed ({'status': the
+        request's own status, 'counts', times}); raises SilError with
+        SIL_ETIMEOUT if it has not completed within timeout_ms."""
         res = sil_request_result()
         st = _lib.sil_server_wait(self.handle, rid, int(timeout_ms), ctypes.byref(res))
-        if st == SIL_ETIMEOUT:
+        if st != SIL_OK:
             raise SilError(st, (_lib.sil_last_error() or b"").decode())
         self._keep.pop(rid, None)
-        out = self._result(res)
-        out["status"] = st
-        return out
+        return self._result(res)
 
     def poll(self, rid: int):
+        """The result if request rid has completed, None if not yet;
+        {'status': SIL_EINVAL} for an unknown id."""
         res = sil_request_result()
         st = _lib.sil_server_poll(self.handle, rid, ctypes.byref(res))
         if st == SIL_EBUSY:
             return None
+        if st != SIL_OK:
+            return {"id": rid, "status": st}
         self._keep.pop(rid, None)
-        out = self._result(res)
-        out["status"] = st
-        return out
+        return self._result(res)
 
     def cancel(self, rid: int) -> int:
         return _lib.sil_server_cancel(self.handle, rid)
+
+    def stats(self) -> dict:
+        """{'kernel_launches', 'chips_published'} so far."""
+        a, b = _I64(0), _I64(0)
+        check(_lib.sil_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return {"kernel_launches": a.value, "chips_published": b.value}
+
+    def set_fault(self, skip_ready: bool) -> None:
+        """Test hook: the next published request never gets its ready word
+        (its chips' bounded device waits run out; it ends with SIL_ETIMEOUT)."""
+        check(_lib.sil_server_set_fault(self.handle, int(bool(skip_ready))))
 
     def close(self):
         if self.handle:

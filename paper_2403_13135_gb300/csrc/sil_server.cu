@@ -1,19 +1,30 @@
-// sil_server.cu -- continuous-batching labelling server (host runtime).
+// sil_server.cu -- continuous-batching labelling server: a device-resident
+// request ring read by a persistent kernel, and the host runtime around it.
 //
-// Requests carry HOST images.  A worker thread admits them in arrival order
-// while a request slot and room in a device arena are free, copies each
-// image into the arena on an ingest stream, and launches the persistent
-// batch kernel over every admitted request whose copy has been issued
-// (waiting on their copy events, not on the host).  Results go back on an
-// egress stream; completion is observed through events.  Requests that
-// arrive while others are on the GPU are admitted as memory frees up, and
-// their copies overlap the running kernels.  The paper's equivalent is the
-// Spark driver distributing images to executors and collecting the labelled
-// results (Sec. III-B "PySpark Map-Reduce").
+// Host (one worker thread): admits requests in arrival order while a slot
+// and room in a device arena are free, copies each image into the arena on
+// the ingest stream and then publishes the request to the ring with more
+// copies on the same stream (so they land after the image): the slot's
+// descriptor with its ready word, its counts zeroed, a log entry (sequence
+// number, chip count, slot) and the ring's count of published requests.  It keeps one
+// persistent kernel running while there is published work, polls the
+// completion words the kernel writes into host-mapped memory, and copies
+// each finished request's labels, counts and status back on the egress
+// stream.
 //
-// No kernel waits on the host or on another kernel: the only waits are host
-// waits on CUDA events and condition variables, all of them bounded by the
-// caller's timeout.
+// Device (k_served): every CTA claims its next chip from the oldest
+// published request that has chips left (an atomic counter per request; an
+// exhausted request moves the ring's cursor on by a compare-and-swap),
+// checks the request's ready word, labels the chip with the same per-chip
+// code as every other entry point, and counts it done; the CTA that
+// finishes a request's last chip writes its completion word.  Every wait is
+// bounded: no published chip for idle_ns -> the CTA exits; a ready word
+// that does not arrive within ready_ns -> the request is marked timed out
+// and its chips are skipped.
+//
+// The paper's equivalent is the Spark driver distributing images to
+// executors and collecting the labelled results (Sec. III-B "PySpark
+// Map-Reduce").
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,14 +41,178 @@
 #include <vector>
 
 #include "sil.h"
-#include "sil_batch.h"
+#include "sil_chip.cuh"
 #include "sil_common.h"
+#include "sil_generic.cuh"
 
 namespace sil {
 sil_status check_request(const void* img, int64_t H, int64_t W, int64_t pitch,
                          sil_dtype dt, const uint8_t* labels, int64_t lpitch,
                          const uint64_t* counts);
+size_t resident_smem_bytes(int dt, bool hs);
+int device_sm_count();
+
+// ---------------------------------------------------------------------------
+// Ring layout (device memory unless stated).
+// ---------------------------------------------------------------------------
+struct RingCtl {
+  unsigned long long pub;   // requests published (written by the ingest stream)
+  unsigned long long cur;   // oldest request that may still have unclaimed chips
+  unsigned int err;         // log entries found missing (0 in normal operation)
+};
+// One publication: request sequence number + 1 (0 = never written), its chip
+// count and slot.
+struct LogEntry {
+  unsigned long long seq1;
+  unsigned int c;
+  unsigned int slot;
+};
+// One request slot: descriptor, the claim word (high half: the low 32 bits
+// of seq + 1 of the request it belongs to, low half: chips claimed), the
+// ready word (seq + 1 once the image is in place), chips done, status (1:
+// the ready wait ran out).  Tagging the claim word with the request makes a
+// claim that raced with the slot's reuse by a newer request fail instead of
+// taking that request's chip.
+struct SlotDev {
+  Req req;
+  unsigned long long claimw;
+  unsigned int ready;
+  unsigned int done;
+  unsigned int status;
+  unsigned int pad;
+};
+constexpr int kLogFactor = 4;  // log entries per request slot
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
 }
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int ld_acquire32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int DT, bool HS, bool RESIDENT>
+__global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
+    k_served(RingCtl* ctl, const LogEntry* log, int L, SlotDev* slots, unsigned int* complete,
+             DevParams dp, int chip, long long ready_ns, long long idle_ns) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  __shared__ uint8_t lut[256];
+  __shared__ Req s_req;
+  __shared__ long long s_local;
+  __shared__ int s_slot, s_ok, s_got;
+  __shared__ unsigned int s_c, s_seq32;
+  __shared__ __align__(16) ChipStat st_generic;
+  while (true) {
+    if (threadIdx.x == 0) {
+      // claim a chip: the oldest published request with chips left hands
+      // out its next chip (a per-request counter); an exhausted request
+      // moves the ring's cursor on.  No published chip for idle_ns -> leave.
+      int got = 0;
+      const unsigned long long t0 = gtimer();
+      while (true) {
+        const unsigned long long pub = ld_acquire(&ctl->pub);
+        const unsigned long long cur = ld_acquire(&ctl->cur);
+        if (cur < pub) {
+          const LogEntry* le = &log[cur % (unsigned long long)L];
+          if (ld_acquire(&le->seq1) != cur + 1) {
+            atomicAdd(&ctl->err, 1u);  // overwritten: cannot happen with <= L requests in flight
+            break;
+          }
+          const unsigned int c = *reinterpret_cast<const volatile unsigned int*>(&le->c);
+          const unsigned int slot = *reinterpret_cast<const volatile unsigned int*>(&le->slot);
+          const unsigned long long tag = (cur + 1ull) << 32;
+          unsigned long long w = ld_acquire(&slots[slot].claimw);
+          bool exhausted = false;
+          while ((w & ~0xffffffffull) == (tag & 0xffffffff00000000ull)) {
+            const unsigned int k = unsigned(w);
+            if (k >= c) {
+              exhausted = true;
+              break;
+            }
+            const unsigned long long seen = atomicCAS(&slots[slot].claimw, w, w + 1ull);
+            if (seen == w) {
+              got = 1;
+              s_slot = int(slot);
+              s_local = (long long)k;
+              s_c = c;
+              s_seq32 = unsigned(cur + 1);
+              break;
+            }
+            w = seen;
+            if ((long long)(gtimer() - t0) > idle_ns + ready_ns) break;
+          }
+          if (got) break;
+          // every chip of it is claimed, or the slot already holds a newer
+          // request (this cursor value is stale): move the cursor on
+          if (exhausted || (w >> 32) != ((cur + 1ull) & 0xffffffffull)) atomicCAS(&ctl->cur, cur, cur + 1ull);
+        } else {
+          if ((long long)(gtimer() - t0) > idle_ns) break;
+          __nanosleep(1000);
+        }
+        if ((long long)(gtimer() - t0) > idle_ns + ready_ns) break;  // bounded in every case
+      }
+      s_got = got;
+      s_ok = 0;
+      if (got) {
+        SlotDev* sd = &slots[s_slot];
+        // the request's image is in place once its ready word is set
+        bool ok = ld_acquire32(&sd->status) == 0;
+        const unsigned long long t1 = gtimer();
+        while (ok && ld_acquire32(&sd->ready) != s_seq32) {
+          if (ld_acquire32(&sd->status) != 0) {
+            ok = false;  // another CTA's wait for this request ran out
+          } else if ((long long)(gtimer() - t1) > ready_ns) {
+            atomicExch(&sd->status, 1u);
+            ok = false;
+          } else {
+            __nanosleep(2000);
+          }
+        }
+        s_ok = ok && ld_acquire32(&sd->status) == 0;
+        if (s_ok) {
+          // the descriptor through L2 (an earlier request's copy of this
+          // slot may still sit in this SM's L1)
+          const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&sd->req);
+          unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_req);
+          for (int w = 0; w < int(sizeof(Req) / 8); ++w) dst[w] = __ldcg(src + w);
+        }
+      }
+    }
+    __syncthreads();
+    if (!s_got) break;
+    if (s_ok) {
+      const Req r = s_req;
+      const int64_t cy = s_local / r.gx, cx = s_local - cy * r.gx;
+      if (RESIDENT) {
+        ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
+        label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, lut);
+      } else {
+        label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st_generic, lut);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      SlotDev* sd = &slots[s_slot];
+      __threadfence();  // this chip's labels and counts before its done count
+      const unsigned int old = atomicAdd(&sd->done, 1u);
+      if (old + 1u == s_c) {
+        __threadfence();  // every chip's results before the completion word
+        *reinterpret_cast<volatile unsigned int*>(&complete[s_slot]) = s_seq32;
+        __threadfence_system();
+      }
+    }
+  }
+}
+
+}  // namespace sil
 
 using namespace sil;
 
@@ -61,7 +236,6 @@ class Arena {
         const size_t at = it->first + bytes;
         free_.erase(it);
         if (rest) free_[at] = rest;
-        used_ += bytes;
         return true;
       }
     }
@@ -69,7 +243,6 @@ class Arena {
   }
   void release(size_t off, size_t bytes) {
     bytes = (bytes + 255) & ~size_t(255);
-    used_ -= bytes;
     auto it = free_.emplace(off, bytes).first;
     auto nx = std::next(it);
     if (nx != free_.end() && it->first + it->second == nx->first) {
@@ -88,11 +261,10 @@ class Arena {
 
  private:
   size_t size_;
-  size_t used_ = 0;
   std::map<size_t, size_t> free_;
 };
 
-enum class St { kPending, kAdmitted, kRunning, kDone, kCanceled };
+enum class St { kPending, kPublished, kCopyBack, kDone, kCanceled };
 
 struct Request {
   int64_t id = 0;
@@ -104,15 +276,21 @@ struct Request {
   int gx = 0, gy = 0;
   // device layout inside the arena
   size_t off = 0, bytes = 0, dpitch = 0, o_lab = 0, o_cnt = 0, o_cc = 0;
-  int slot = -1;  // index into the pinned result area
+  int slot = -1;
+  uint64_t seq = 0;
   St st = St::kPending;
   sil_status status = SIL_OK;
   uint64_t counts[4] = {0, 0, 0, 0};
   double t_submit = 0, t_admit = 0, t_done = 0;
-  cudaEvent_t ev_in = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_done = nullptr;
 };
 
-constexpr int kDescSlots = 8;
+// Pinned host staging of one slot's copies (stable until the slot is reused).
+struct SlotHost {
+  SlotDev desc;
+  uint64_t counts[4];     // results copied back
+  unsigned int status;    // the slot's status word copied back
+};
 
 }  // namespace
 
@@ -123,34 +301,41 @@ struct sil_server {
   DevParams dp{};
   int bpp = 3;
   int grid = 1;
+  size_t smem = 0;
   uint8_t* arena_mem = nullptr;
   std::unique_ptr<Arena> arena;
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
-  // pinned per-slot results: counts (4 x u64)
-  uint64_t* h_counts = nullptr;
+  // ring
+  RingCtl* d_ctl = nullptr;
+  LogEntry* d_log = nullptr;
+  SlotDev* d_slots = nullptr;
+  unsigned int* h_complete = nullptr;  // host-mapped, written by the kernel
+  unsigned int* d_complete = nullptr;  // its device alias
+  SlotHost* h_slot = nullptr;          // pinned staging per slot
+  LogEntry* h_log = nullptr;           // pinned staging per log entry
+  unsigned long long* h_tail = nullptr;  // pinned staging of the published request count, per log entry
+  int L = 0;
+  uint64_t next_seq = 0;    // next publication
+  uint64_t published = 0;   // chips published
+  cudaEvent_t ev_kernel = nullptr;
+  bool kernel_live = false;
+  int64_t launches = 0;  // kernel launches so far
+  std::atomic<int> skip_ready{0};  // test hook
   std::vector<int> free_slots;
-  // descriptor ring for batch launches
-  Req* d_reqs[kDescSlots] = {};
-  int64_t* d_prefix[kDescSlots] = {};
-  unsigned long long* d_head[kDescSlots] = {};
-  Req* h_reqs[kDescSlots] = {};
-  int64_t* h_prefix[kDescSlots] = {};
-  cudaEvent_t desc_done[kDescSlots] = {};
-  int desc_next = 0;
+  Request* by_slot[4096] = {};
 
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> pending;
-  std::vector<Request*> admitted;  // copy issued, not yet launched
-  std::vector<Request*> running;
+  std::vector<Request*> running;  // published or copying back
   std::unordered_map<int64_t, std::unique_ptr<Request>> all;
   int64_t next_id = 1;
   bool stop = false;
   std::thread worker;
-  std::atomic<int> worker_error{0};
 
   void run();
   void finish(Request* r, sil_status st);
+  cudaError_t launch();
 };
 
 namespace {
@@ -161,7 +346,7 @@ size_t request_bytes(const sil_server* s, Request* r) {
   size_t off = r->dpitch * size_t(r->H);
   off = (off + 255) & ~size_t(255);
   r->o_lab = off;
-  if (r->labels && s->cfg.want_labels) off += size_t(r->W * r->H);
+  off += size_t(r->W * r->H);  // labels are always written (the kernel labels whole chips)
   off = (off + 255) & ~size_t(255);
   r->o_cnt = off;
   off += 32;
@@ -171,7 +356,59 @@ size_t request_bytes(const sil_server* s, Request* r) {
   return off;
 }
 
+template <int DT, bool HS, bool RES>
+cudaError_t launch_served(const sil_server* s, cudaStream_t st) {
+  k_served<DT, HS, RES><<<s->grid, kThreadsNarrow, RES ? s->smem : 0, st>>>(
+      s->d_ctl, s->d_log, s->L, s->d_slots, s->d_complete, s->dp, s->params.chip,
+      (long long)s->cfg.ready_timeout_ms * 1000000ll, (long long)s->cfg.idle_timeout_us * 1000ll);
+  return cudaGetLastError();
+}
+
+template <int DT, bool HS, bool RES>
+cudaError_t prepare_served(size_t smem, int* per_sm) {
+  cudaError_t e = cudaSuccess;
+  if (RES)
+    e = cudaFuncSetAttribute(k_served<DT, HS, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_served<DT, HS, RES>, kThreadsNarrow,
+                                                      RES ? smem : 0);
+  return e;
+}
+
+// (dt, H/S, resident) -> the kernel instance
+template <template <int, bool, bool> class F, class... A>
+cudaError_t dispatch_served(int dt, bool hs, bool res, A... a) {
+  if (dt == SIL_U8) {
+    if (hs) return res ? F<SIL_U8, true, true>::run(a...) : F<SIL_U8, true, false>::run(a...);
+    return res ? F<SIL_U8, false, true>::run(a...) : F<SIL_U8, false, false>::run(a...);
+  }
+  if (hs) return res ? F<SIL_U16, true, true>::run(a...) : F<SIL_U16, true, false>::run(a...);
+  return res ? F<SIL_U16, false, true>::run(a...) : F<SIL_U16, false, false>::run(a...);
+}
+template <int DT, bool HS, bool RES>
+struct LaunchServed {
+  static cudaError_t run(const sil_server* s, cudaStream_t st) {
+    return launch_served<DT, HS, RES>(s, st);
+  }
+};
+template <int DT, bool HS, bool RES>
+struct PrepareServed {
+  static cudaError_t run(size_t smem, int* per_sm) { return prepare_served<DT, HS, RES>(smem, per_sm); }
+};
+
 }  // namespace
+
+cudaError_t sil_server::launch() {
+  cudaError_t e = dispatch_served<LaunchServed>(int(dt), dp.need_hs != 0, params.chip <= kResidentChip,
+                                                static_cast<const sil_server*>(this), s_comp);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_kernel, s_comp);
+  if (e == cudaSuccess) {
+    kernel_live = true;
+    ++launches;
+  }
+  return e;
+}
 
 void sil_server::finish(Request* r, sil_status st) {
   r->status = st;
@@ -183,9 +420,12 @@ void sil_server::run() {
   cudaSetDevice(cfg.device);
   std::unique_lock<std::mutex> lk(mu);
   while (true) {
-    if (stop && pending.empty() && admitted.empty() && running.empty()) break;
+    if (stop && pending.empty() && running.empty()) break;
     bool progressed = false;
-    // 1. admission: arrival order, while a slot and arena room are free
+    cudaError_t e = cudaSuccess;
+    // 1. admission in arrival order, then publication on the ingest stream:
+    //    image, slot descriptor (+ ready word), counts = 0, log entry,
+    //    published chip count -- in that order, all by the copy engines
     while (!pending.empty() && !free_slots.empty()) {
       Request* r = pending.front();
       size_t off;
@@ -194,101 +434,122 @@ void sil_server::run() {
       r->off = off;
       r->slot = free_slots.back();
       free_slots.pop_back();
-      r->st = St::kAdmitted;
       r->t_admit = now_ms();
-      cudaError_t e = cudaMemcpy2DAsync(arena_mem + r->off, r->dpitch, r->img, r->pitch,
-                                        r->W * bpp, r->H, cudaMemcpyHostToDevice, s_in);
-      if (e == cudaSuccess) e = cudaEventRecord(r->ev_in, s_in);
-      if (e != cudaSuccess) {
-        arena->release(r->off, r->bytes);
-        free_slots.push_back(r->slot);
-        finish(r, SIL_ECUDA);
-        cv_done.notify_all();
+      r->seq = next_seq++;
+      by_slot[r->slot] = r;
+      const int64_t chips = int64_t(r->gx) * r->gy;
+      SlotHost& hs = h_slot[r->slot];
+      memset(&hs.desc, 0, sizeof(hs.desc));
+      Req& q = hs.desc.req;
+      q.img = arena_mem + r->off;
+      q.H = r->H;
+      q.W = r->W;
+      q.pitch = int64_t(r->dpitch);
+      q.labels = arena_mem + r->off + r->o_lab;
+      q.lpitch = r->W;
+      q.counts = reinterpret_cast<unsigned long long*>(arena_mem + r->off + r->o_cnt);
+      q.chip_counts = reinterpret_cast<uint32_t*>(arena_mem + r->off + r->o_cc);
+      q.gx = r->gx;
+      q.gy = r->gy;
+      q.chip_begin = int64_t(published);
+      hs.desc.ready = skip_ready.exchange(0) ? 0u : unsigned(r->seq + 1);
+      hs.desc.claimw = uint64_t(unsigned(r->seq + 1)) << 32;
+      hs.desc.done = 0;
+      hs.desc.status = 0;
+      const int li = int(r->seq % uint64_t(L));
+      h_log[li].seq1 = r->seq + 1;
+      h_log[li].c = unsigned(chips);
+      h_log[li].slot = unsigned(r->slot);
+      published += uint64_t(chips);
+      h_tail[li] = r->seq + 1;  // requests published
+      h_complete[r->slot] = 0;
+      e = cudaMemcpy2DAsync(arena_mem + r->off, r->dpitch, r->img, r->pitch, r->W * bpp, r->H,
+                            cudaMemcpyHostToDevice, s_in);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&d_slots[r->slot], &hs.desc, sizeof(SlotDev), cudaMemcpyHostToDevice, s_in);
+      // (a copy, not a memset: a memset is a kernel, which would wait for
+      // the persistent kernel's CTAs to leave the SMs)
+      memset(hs.counts, 0, sizeof(hs.counts));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(arena_mem + r->off + r->o_cnt, hs.counts, 32, cudaMemcpyHostToDevice, s_in);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&d_log[li], &h_log[li], sizeof(LogEntry), cudaMemcpyHostToDevice, s_in);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&d_ctl->pub, &h_tail[li], sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                            s_in);
+      r->st = St::kPublished;
+      running.push_back(r);
+      progressed = true;
+      if (e != cudaSuccess) break;
+    }
+    // 2. keep a kernel running while published chips may be unclaimed
+    if (e == cudaSuccess && kernel_live && cudaEventQuery(ev_kernel) == cudaSuccess) kernel_live = false;
+    if (e == cudaSuccess && !kernel_live) {
+      bool work = false;
+      for (const Request* r : running)
+        if (r->st == St::kPublished) work = true;
+      if (work) {
+        // the kernel has ended (its CTAs found no chip for idle_timeout_us)
+        // while published requests are unfinished: start it again (the
+        // ring's cursor and claim words carry over)
+        e = launch();
+        progressed = true;
+      }
+    }
+    // 3. completions: the kernel's completion word -> copy the results back
+    for (size_t i = 0; i < running.size() && e == cudaSuccess; ++i) {
+      Request* r = running[i];
+      if (r->st != St::kPublished) continue;
+      if (*reinterpret_cast<volatile unsigned int*>(&h_complete[r->slot]) != unsigned(r->seq + 1))
+        continue;
+      SlotHost& hs = h_slot[r->slot];
+      if (r->labels && cfg.want_labels)
+        e = cudaMemcpy2DAsync(r->labels, r->lpitch, arena_mem + r->off + r->o_lab, r->W, r->W, r->H,
+                              cudaMemcpyDeviceToHost, s_out);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs.counts, arena_mem + r->off + r->o_cnt, 32, cudaMemcpyDeviceToHost, s_out);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hs.status, &d_slots[r->slot].status, 4, cudaMemcpyDeviceToHost, s_out);
+      if (e == cudaSuccess && r->chip_counts)
+        e = cudaMemcpyAsync(r->chip_counts, arena_mem + r->off + r->o_cc, size_t(r->gx) * r->gy * 16,
+                            cudaMemcpyDeviceToHost, s_out);
+      if (e == cudaSuccess) e = cudaEventRecord(r->ev_done, s_out);
+      r->st = St::kCopyBack;
+      progressed = true;
+    }
+    bool done_any = false;
+    for (size_t i = 0; i < running.size() && e == cudaSuccess;) {
+      Request* r = running[i];
+      if (r->st != St::kCopyBack) {
+        ++i;
         continue;
       }
-      admitted.push_back(r);
-      progressed = true;
-    }
-    // 2. launch one persistent kernel over the admitted requests
-    if (!admitted.empty()) {
-      const int nb = std::min<int>(int(admitted.size()), std::max(1, cfg.max_batch));
-      std::vector<Request*> batch(admitted.begin(), admitted.begin() + nb);
-      admitted.erase(admitted.begin(), admitted.begin() + nb);
-      const int ds = desc_next;
-      desc_next = (desc_next + 1) % kDescSlots;
-      lk.unlock();
-      cudaEventSynchronize(desc_done[ds]);  // previous use of this slot done
-      Req* hr = h_reqs[ds];
-      int64_t* hp = h_prefix[ds];
-      hp[0] = 0;
-      for (int i = 0; i < nb; ++i) {
-        Request* r = batch[i];
-        Req& q = hr[i];
-        q.img = arena_mem + r->off;
-        q.H = r->H;
-        q.W = r->W;
-        q.pitch = int64_t(r->dpitch);
-        q.labels = (r->labels && cfg.want_labels) ? arena_mem + r->off + r->o_lab : nullptr;
-        q.lpitch = r->W;
-        q.counts = reinterpret_cast<unsigned long long*>(arena_mem + r->off + r->o_cnt);
-        q.chip_counts = reinterpret_cast<uint32_t*>(arena_mem + r->off + r->o_cc);
-        q.gx = r->gx;
-        q.gy = r->gy;
-        q.chip_begin = hp[i];
-        hp[i + 1] = hp[i] + int64_t(r->gx) * r->gy;
-        cudaStreamWaitEvent(s_comp, r->ev_in, 0);
-      }
-      cudaError_t e = cudaMemcpyAsync(d_reqs[ds], hr, sizeof(Req) * nb, cudaMemcpyHostToDevice, s_comp);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_prefix[ds], hp, sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s_comp);
-      if (e == cudaSuccess) {
-        BatchLaunch b{d_reqs[ds], d_prefix[ds], nb, int(dt), dp, params.chip, d_head[ds],
-                      int(std::min<int64_t>(hp[nb], grid)), 1};
-        e = launch_batch(b, s_comp);
-      }
-      if (e == cudaSuccess) e = cudaEventRecord(desc_done[ds], s_comp);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, desc_done[ds], 0);
-      for (int i = 0; i < nb && e == cudaSuccess; ++i) {
-        Request* r = batch[i];
-        if (r->labels && cfg.want_labels)
-          e = cudaMemcpy2DAsync(r->labels, r->lpitch, arena_mem + r->off + r->o_lab, r->W, r->W,
-                                r->H, cudaMemcpyDeviceToHost, s_out);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(h_counts + 4 * r->slot, arena_mem + r->off + r->o_cnt, 32,
-                              cudaMemcpyDeviceToHost, s_out);
-        if (e == cudaSuccess && r->chip_counts)
-          e = cudaMemcpyAsync(r->chip_counts, arena_mem + r->off + r->o_cc,
-                              size_t(r->gx) * r->gy * 16, cudaMemcpyDeviceToHost, s_out);
-        if (e == cudaSuccess) e = cudaEventRecord(r->ev_done, s_out);
-      }
-      lk.lock();
-      for (Request* r : batch) {
-        if (e != cudaSuccess) {
-          worker_error = 1;
-          finish(r, SIL_ECUDA);
-          continue;
-        }
-        r->st = St::kRunning;
-        running.push_back(r);
-      }
-      if (e != cudaSuccess) cv_done.notify_all();
-      progressed = true;
-    }
-    // 3. completions
-    bool done_any = false;
-    for (size_t i = 0; i < running.size();) {
-      Request* r = running[i];
       const cudaError_t q = cudaEventQuery(r->ev_done);
       if (q == cudaErrorNotReady) {
         ++i;
         continue;
       }
-      if (q == cudaSuccess) memcpy(r->counts, h_counts + 4 * r->slot, 32);
+      const SlotHost& hs = h_slot[r->slot];
+      memcpy(r->counts, hs.counts, 32);
+      sil_status st = q == cudaSuccess ? SIL_OK : SIL_ECUDA;
+      if (st == SIL_OK && hs.status != 0) st = SIL_ETIMEOUT;
       arena->release(r->off, r->bytes);
       free_slots.push_back(r->slot);
-      finish(r, q == cudaSuccess ? SIL_OK : SIL_ECUDA);
+      by_slot[r->slot] = nullptr;
+      finish(r, st);
       running[i] = running.back();
       running.pop_back();
+      done_any = true;
+    }
+    if (e != cudaSuccess) {
+      // a CUDA failure ends every request in flight
+      for (Request* r : running) {
+        arena->release(r->off, r->bytes);
+        free_slots.push_back(r->slot);
+        finish(r, SIL_ECUDA);
+      }
+      running.clear();
+      cudaGetLastError();
       done_any = true;
     }
     if (done_any) {
@@ -296,8 +557,9 @@ void sil_server::run() {
       progressed = true;
     }
     if (!progressed) {
-      // nothing to admit or launch: sleep until new work or a short poll tick
-      cv_work.wait_for(lk, std::chrono::microseconds(running.empty() ? 2000 : 50));
+      // nothing to admit, launch or complete: sleep until new work or a
+      // short poll tick (completion words are polled)
+      cv_work.wait_for(lk, std::chrono::microseconds(running.empty() ? 2000 : 20));
     }
   }
 }
@@ -314,6 +576,8 @@ sil_status sil_server_config_default(sil_server_config* cfg) {
   cfg->device_mem_budget = 0;
   cfg->max_batch = 32;
   cfg->want_labels = 1;
+  cfg->ready_timeout_ms = 2000;
+  cfg->idle_timeout_us = 5000;
   return SIL_OK;
 }
 
@@ -333,8 +597,9 @@ sil_status sil_server_create(sil_server** out, const sil_server_config* cfg_in, 
     set_error("sil_server_create: dtype %d", int(dt));
     return SIL_EINVAL;
   }
-  if (cfg.max_inflight < 1 || cfg.max_inflight > 4096 || cfg.max_batch < 1 ||
-      cfg.device_mem_budget < 0) {
+  if (cfg.max_inflight < 1 || cfg.max_inflight > 4096 || cfg.device_mem_budget < 0 ||
+      cfg.ready_timeout_ms < 1 || cfg.ready_timeout_ms > 600000 || cfg.idle_timeout_us < 1 ||
+      cfg.idle_timeout_us > 10000000) {
     set_error("sil_server_create: bad config");
     return SIL_EINVAL;
   }
@@ -353,6 +618,7 @@ sil_status sil_server_create(sil_server** out, const sil_server_config* cfg_in, 
   s->cfg = cfg;
   s->dt = dt;
   s->bpp = dt == SIL_U8 ? 3 : 6;
+  s->L = kLogFactor * cfg.max_inflight;
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(cfg.device);
@@ -367,19 +633,30 @@ sil_status sil_server_create(sil_server** out, const sil_server_config* cfg_in, 
     return SIL_ENOMEM;
   }
   s->arena.reset(new Arena(budget));
-  e = cudaMallocHost(&s->h_counts, sizeof(uint64_t) * 4 * cfg.max_inflight);
-  for (int i = 0; i < cfg.max_inflight; ++i) s->free_slots.push_back(cfg.max_inflight - 1 - i);
-  for (int i = 0; i < kDescSlots && e == cudaSuccess; ++i) {
-    e = cudaMalloc(&s->d_reqs[i], sizeof(Req) * cfg.max_batch);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_prefix[i], sizeof(int64_t) * (cfg.max_batch + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_head[i], sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_reqs[i], sizeof(Req) * cfg.max_batch);
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_prefix[i], sizeof(int64_t) * (cfg.max_batch + 1));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->desc_done[i], cudaEventDisableTiming);
-  }
+  const int R = cfg.max_inflight;
+  for (int i = 0; i < R; ++i) s->free_slots.push_back(R - 1 - i);
+  e = cudaMalloc(&s->d_ctl, sizeof(RingCtl));
+  if (e == cudaSuccess) e = cudaMemset(s->d_ctl, 0, sizeof(RingCtl));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_log, sizeof(LogEntry) * s->L);
+  if (e == cudaSuccess) e = cudaMemset(s->d_log, 0, sizeof(LogEntry) * s->L);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_slots, sizeof(SlotDev) * R);
+  if (e == cudaSuccess) e = cudaMemset(s->d_slots, 0, sizeof(SlotDev) * R);
+  if (e == cudaSuccess) e = cudaHostAlloc(&s->h_complete, sizeof(unsigned int) * R, cudaHostAllocMapped);
+  if (e == cudaSuccess) memset(s->h_complete, 0, sizeof(unsigned int) * R);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_complete), s->h_complete, 0);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_slot, sizeof(SlotHost) * R);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_log, sizeof(LogEntry) * s->L);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_tail, sizeof(unsigned long long) * s->L);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_kernel, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking);
+  int per_sm = 0;
+  if (e == cudaSuccess) {
+    const bool hs = s->dp.need_hs != 0;
+    s->smem = resident_smem_bytes(dt, hs);
+    e = dispatch_served<PrepareServed>(int(dt), hs, s->params.chip <= kResidentChip, s->smem, &per_sm);
+  }
   if (e != cudaSuccess) {
     sil_server* raw = s.release();
     raw->stop = true;
@@ -388,9 +665,7 @@ sil_status sil_server_create(sil_server** out, const sil_server_config* cfg_in, 
     set_error("sil_server_create: %s", cudaGetErrorString(e));
     return SIL_ENOMEM;
   }
-  int sms = 1;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg.device);
-  s->grid = sms * batch_max_ctas_per_sm(dt, s->dp.need_hs != 0, s->params.chip);
+  s->grid = (per_sm > 0 ? per_sm : 1) * device_sm_count();
   cudaSetDevice(prev);
   sil_server* raw = s.release();
   raw->worker = std::thread([raw] { raw->run(); });
@@ -424,9 +699,7 @@ sil_status sil_server_submit(sil_server* srv, const void* img, int64_t H, int64_
               srv->arena->size());
     return SIL_EBUSY;
   }
-  if (cudaEventCreateWithFlags(&r->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming) != cudaSuccess) {
-    if (r->ev_in) cudaEventDestroy(r->ev_in);
+  if (cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming) != cudaSuccess) {
     set_error("sil_server_submit: event creation failed");
     return SIL_ECUDA;
   }
@@ -434,7 +707,6 @@ sil_status sil_server_submit(sil_server* srv, const void* img, int64_t H, int64_
   {
     std::lock_guard<std::mutex> g(srv->mu);
     if (srv->stop) {
-      cudaEventDestroy(r->ev_in);
       cudaEventDestroy(r->ev_done);
       set_error("sil_server_submit: server is shutting down");
       return SIL_ECANCELED;
@@ -461,7 +733,6 @@ static void fill_result(const Request* r, sil_request_result* out) {
 static void release_request(sil_server* srv, int64_t id) {
   auto it = srv->all.find(id);
   if (it == srv->all.end()) return;
-  cudaEventDestroy(it->second->ev_in);
   cudaEventDestroy(it->second->ev_done);
   srv->all.erase(it);
 }
@@ -488,9 +759,8 @@ sil_status sil_server_wait(sil_server* srv, int64_t id, int64_t timeout_ms,
     return SIL_ETIMEOUT;
   }
   fill_result(r, out);
-  const sil_status st = r->status;
   release_request(srv, id);
-  return st == SIL_OK ? SIL_OK : st;
+  return SIL_OK;
 }
 
 sil_status sil_server_poll(sil_server* srv, int64_t id, sil_request_result* out) {
@@ -507,9 +777,8 @@ sil_status sil_server_poll(sil_server* srv, int64_t id, sil_request_result* out)
   Request* r = it->second.get();
   if (r->st != St::kDone && r->st != St::kCanceled) return SIL_EBUSY;
   fill_result(r, out);
-  const sil_status st = r->status;
   release_request(srv, id);
-  return st;
+  return SIL_OK;
 }
 
 sil_status sil_server_cancel(sil_server* srv, int64_t id) {
@@ -536,6 +805,26 @@ sil_status sil_server_cancel(sil_server* srv, int64_t id) {
   return SIL_OK;
 }
 
+sil_status sil_server_stats(sil_server* srv, int64_t* kernel_launches, int64_t* chips_published) {
+  if (!srv) {
+    set_error("sil_server_stats: NULL");
+    return SIL_EINVAL;
+  }
+  std::lock_guard<std::mutex> g(srv->mu);
+  if (kernel_launches) *kernel_launches = srv->launches;
+  if (chips_published) *chips_published = int64_t(srv->published);
+  return SIL_OK;
+}
+
+sil_status sil_server_set_fault(sil_server* srv, int32_t skip_ready) {
+  if (!srv) {
+    set_error("sil_server_set_fault: NULL");
+    return SIL_EINVAL;
+  }
+  srv->skip_ready = skip_ready ? 1 : 0;
+  return SIL_OK;
+}
+
 void sil_server_destroy(sil_server* srv) {
   if (!srv) return;
   {
@@ -550,23 +839,21 @@ void sil_server_destroy(sil_server* srv) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(srv->cfg.device);
+  // the worker leaves when nothing is in flight; the kernel ends on its own
+  // (no work for idle_timeout_us)
   if (srv->s_in) cudaStreamSynchronize(srv->s_in);
   if (srv->s_comp) cudaStreamSynchronize(srv->s_comp);
   if (srv->s_out) cudaStreamSynchronize(srv->s_out);
-  for (auto& kv : srv->all) {
-    cudaEventDestroy(kv.second->ev_in);
-    cudaEventDestroy(kv.second->ev_done);
-  }
+  for (auto& kv : srv->all) cudaEventDestroy(kv.second->ev_done);
   srv->all.clear();
-  for (int i = 0; i < kDescSlots; ++i) {
-    cudaFree(srv->d_reqs[i]);
-    cudaFree(srv->d_prefix[i]);
-    cudaFree(srv->d_head[i]);
-    cudaFreeHost(srv->h_reqs[i]);
-    cudaFreeHost(srv->h_prefix[i]);
-    if (srv->desc_done[i]) cudaEventDestroy(srv->desc_done[i]);
-  }
-  cudaFreeHost(srv->h_counts);
+  cudaFree(srv->d_ctl);
+  cudaFree(srv->d_log);
+  cudaFree(srv->d_slots);
+  cudaFreeHost(srv->h_complete);
+  cudaFreeHost(srv->h_slot);
+  cudaFreeHost(srv->h_log);
+  cudaFreeHost(srv->h_tail);
+  if (srv->ev_kernel) cudaEventDestroy(srv->ev_kernel);
   cudaFree(srv->arena_mem);
   if (srv->s_in) cudaStreamDestroy(srv->s_in);
   if (srv->s_comp) cudaStreamDestroy(srv->s_comp);

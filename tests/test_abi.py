@@ -74,7 +74,7 @@ def test_status_strings(sil):
     for s in range(7):
         assert sil.sil_status_string(s)
     assert sil.sil_status_string(99) == b"unknown status"
-    assert sil.sil_version() == 1
+    assert sil.sil_version() == 2
 
 
 def test_null_arguments_rejected_without_gpu(sil):

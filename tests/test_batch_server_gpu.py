@@ -160,6 +160,54 @@ def test_server_alone_equals_mix_and_oracle(sil):
         assert r["t_submit_ms"] <= r["t_admit_ms"] <= r["t_done_ms"]
 
 
+def test_server_ring_takes_requests_while_running(sil):
+    """Requests submitted back to back are published to the device ring and
+    taken up by the running persistent kernel: far fewer kernel launches than
+    requests, every result equal to the oracle's."""
+    imgs = _tiles(40, seed=6)
+    with sil.Server(max_inflight=64, idle_timeout_us=200000) as srv:
+        outs = []
+        for im in imgs:
+            lab = np.empty(im.shape[:2], np.uint8)
+            outs.append((srv.submit(im, lab), lab))
+        res = [(srv.wait(i, 60000), lab) for i, lab in outs]
+        st = srv.stats()
+    assert st["kernel_launches"] < len(imgs) // 2, st
+    assert st["chips_published"] == sum(-(-im.shape[0] // 256) * -(-im.shape[1] // 256) for im in imgs)
+    for im, (r, lab) in zip(imgs, res):
+        assert r["status"] == sil.SIL_OK
+        ol, oc, _, _ = oracle.label(im)
+        assert np.array_equal(lab, ol) and r["counts"] == [int(x) for x in oc]
+
+
+def test_server_ring_ready_wait_runs_out(sil):
+    """Failure detection without a GPU fault: the test hook publishes a
+    request without its ready word, so the kernel's bounded wait for it runs
+    out (ready_timeout_ms) and it ends with SIL_ETIMEOUT; the requests before
+    and after it, and later ones on the same server, are labelled correctly."""
+    import time
+    imgs = _tiles(4, seed=7)
+    with sil.Server(max_inflight=8, ready_timeout_ms=300) as srv:
+        la = np.empty(imgs[0].shape[:2], np.uint8)
+        ra = srv.wait(srv.submit(imgs[0], la), 60000)
+        srv.set_fault(True)
+        t0 = time.monotonic()
+        rb_id = srv.submit(imgs[1], np.empty(imgs[1].shape[:2], np.uint8))
+        lc = np.empty(imgs[2].shape[:2], np.uint8)
+        rc_id = srv.submit(imgs[2], lc)
+        rb = srv.wait(rb_id, 60000)
+        tb = time.monotonic() - t0
+        rc = srv.wait(rc_id, 60000)
+        ld = np.empty(imgs[3].shape[:2], np.uint8)
+        rd = srv.wait(srv.submit(imgs[3], ld), 60000)
+    assert rb["status"] == sil.SIL_ETIMEOUT
+    assert 0.3 <= tb < 30, tb
+    for im, r, lab in ((imgs[0], ra, la), (imgs[2], rc, lc), (imgs[3], rd, ld)):
+        assert r["status"] == sil.SIL_OK
+        ol, oc, _, _ = oracle.label(im)
+        assert np.array_equal(lab, ol) and r["counts"] == [int(x) for x in oc]
+
+
 def test_server_faults_are_reported(sil):
     """Host-side failures: a request that can never fit the memory budget,
     an invalid request, cancelling a queued request, a wait that runs out,
