@@ -117,6 +117,10 @@ __global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
       // moves the ring's cursor on.  No published chip for idle_ns -> leave.
       int got = 0;
       const unsigned long long t0 = gtimer();
+      // idle polls back off from 1 to 32 us: a few hundred CTAs polling the
+      // ring's two control words every microsecond load one L2 line hard
+      // enough to slow the chips being labelled and the copies
+      unsigned int backoff = 1000;
       while (true) {
         const unsigned long long pub = ld_acquire(&ctl->pub);
         const unsigned long long cur = ld_acquire(&ctl->cur);
@@ -155,7 +159,8 @@ __global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
           if (exhausted || (w >> 32) != ((cur + 1ull) & 0xffffffffull)) atomicCAS(&ctl->cur, cur, cur + 1ull);
         } else {
           if ((long long)(gtimer() - t0) > idle_ns) break;
-          __nanosleep(1000);
+          __nanosleep(backoff);
+          backoff = backoff < 32000u ? 2u * backoff : 32000u;
         }
         if ((long long)(gtimer() - t0) > idle_ns + ready_ns) break;  // bounded in every case
       }
@@ -340,10 +345,14 @@ struct sil_server {
 
 namespace {
 
+// Device layout of a request: the image keeps the host's row pitch, so it
+// arrives by one plain copy of its bytes (a pitched copy may run as a
+// kernel, which would wait for the persistent kernel's CTAs to leave the
+// SMs); labels at W bytes per row (one plain copy back when the caller's
+// label rows are dense too), counts, chip counts.
 size_t request_bytes(const sil_server* s, Request* r) {
-  const int64_t row = r->W * s->bpp;
-  r->dpitch = size_t((row + 127) / 128 * 128);
-  size_t off = r->dpitch * size_t(r->H);
+  r->dpitch = size_t(r->pitch);
+  size_t off = size_t(r->H - 1) * r->dpitch + size_t(r->W) * s->bpp;
   off = (off + 255) & ~size_t(255);
   r->o_lab = off;
   off += size_t(r->W * r->H);  // labels are always written (the kernel labels whole chips)
@@ -355,6 +364,10 @@ size_t request_bytes(const sil_server* s, Request* r) {
   off += size_t(r->gx) * r->gy * 16;
   return off;
 }
+
+}  // namespace
+
+namespace {
 
 template <int DT, bool HS, bool RES>
 cudaError_t launch_served(const sil_server* s, cudaStream_t st) {
@@ -463,8 +476,8 @@ void sil_server::run() {
       published += uint64_t(chips);
       h_tail[li] = r->seq + 1;  // requests published
       h_complete[r->slot] = 0;
-      e = cudaMemcpy2DAsync(arena_mem + r->off, r->dpitch, r->img, r->pitch, r->W * bpp, r->H,
-                            cudaMemcpyHostToDevice, s_in);
+      e = cudaMemcpyAsync(arena_mem + r->off, r->img, size_t(r->H - 1) * r->dpitch + size_t(r->W) * bpp,
+                          cudaMemcpyHostToDevice, s_in);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(&d_slots[r->slot], &hs.desc, sizeof(SlotDev), cudaMemcpyHostToDevice, s_in);
       // (a copy, not a memset: a memset is a kernel, which would wait for
@@ -503,9 +516,14 @@ void sil_server::run() {
       if (*reinterpret_cast<volatile unsigned int*>(&h_complete[r->slot]) != unsigned(r->seq + 1))
         continue;
       SlotHost& hs = h_slot[r->slot];
-      if (r->labels && cfg.want_labels)
-        e = cudaMemcpy2DAsync(r->labels, r->lpitch, arena_mem + r->off + r->o_lab, r->W, r->W, r->H,
+      if (r->labels && cfg.want_labels) {
+        if (r->lpitch == r->W)
+          e = cudaMemcpyAsync(r->labels, arena_mem + r->off + r->o_lab, size_t(r->W) * r->H,
                               cudaMemcpyDeviceToHost, s_out);
+        else
+          e = cudaMemcpy2DAsync(r->labels, r->lpitch, arena_mem + r->off + r->o_lab, r->W, r->W, r->H,
+                                cudaMemcpyDeviceToHost, s_out);
+      }
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(hs.counts, arena_mem + r->off + r->o_cnt, 32, cudaMemcpyDeviceToHost, s_out);
       if (e == cudaSuccess)
@@ -560,6 +578,11 @@ void sil_server::run() {
       // nothing to admit, launch or complete: sleep until new work or a
       // short poll tick (completion words are polled)
       cv_work.wait_for(lk, std::chrono::microseconds(running.empty() ? 2000 : 20));
+    } else {
+      // let submit / wait / poll in between busy iterations
+      lk.unlock();
+      std::this_thread::yield();
+      lk.lock();
     }
   }
 }
