@@ -62,7 +62,7 @@ def head_backward(x, w, dz):
     """1x1 head: scores = x . w^T + b; returns dx, dw [3, F, 1, 1], db."""
     w2 = np.asarray(w, np.float64).reshape(w.shape[0], w.shape[1])
     dx = dz @ w2
-    dw = np.einsum("...k,...c->kc", dz, x).reshape(w.shape)
+    dw = (dz.reshape(-1, dz.shape[-1]).T @ np.asarray(x, np.float64).reshape(-1, x.shape[-1])).reshape(w.shape)
     db = dz.reshape(-1, dz.shape[-1]).sum(axis=0)
     return dx, dw, db
 
