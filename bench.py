@@ -740,6 +740,142 @@ def run_unet(args):
     return 0
 
 
+def _train_launches(shapes, D, F, B):
+    """This library's kernel launches in one training step (forward,
+    loss, backward, Adam and re-packing; the cuBLAS weight-gradient GEMMs
+    are library kernels and not counted)."""
+    nl = len(shapes)
+    res = [256 >> l for l in range(D)] + [256 >> D]
+    col_need, convs = 0, []
+    for i, (shape, kind) in enumerate(shapes):
+        if kind == 0:
+            if i < 2 * D:
+                H = res[i // 2]
+            elif i < 2 * D + 2:
+                H = res[D]
+            else:
+                H = res[D - 1 - (i - 2 * D - 2) // 3]
+            cp = max(8, shape[1])
+            convs.append(B * H * H * 9 * cp)
+            col_need = max(col_need, B * H * H * 9 * cp)
+    cap = min(col_need, 1 << 29)
+    n = 1 + (nl - 1)                       # forward: input preparation + every layer
+    n += 5                                 # count, loss, its sum, head backward, its sum
+    n += sum(-(-c // cap) for c in convs)  # im2col chunks
+    n += nl - 1                            # weight gradients to PyTorch layout
+    n += (nl - 1) - 1                      # dgrad of every layer but the first
+    n += 2 * D                             # space-to-depth and pool backward per level
+    n += 1 + (nl - 1) + (nl - 2)           # Adam, forward and dgrad weight packing
+    return n
+
+
+def run_train(args):
+    """One data-parallel training step of the U-Net (Sec. III-C: Adam,
+    categorical cross-entropy, batch 32 per GPU) on auto-labelled chips of
+    the seeded scene: forward, loss, backward, gradient averaging (none on
+    one GPU), Adam, weight re-packing.  Device-resident timing (tensor-core
+    roofline on 3x the forward FLOPs); end to end with the chips and labels
+    copied in and the loss copied out every step."""
+    import torch
+    import paper_2403_13135_gb300 as sil
+    import synth
+    F, D, B = args.unet_width, args.unet_depth, args.train_batch
+    img, _ = synth.full_scene(1, SIDE)
+    scene_dev = torch.from_numpy(img).cuda()
+    lab_scene, _, _ = sil.label(scene_dev)              # the auto-labels
+    chips_h = synth.chips_from_scene(img, B, seed=3)
+    lab_h = synth.chips_from_scene(lab_scene.cpu().numpy()[..., None], B, seed=3)[..., 0].copy()
+    del img, scene_dev, lab_scene
+    wts = synth.unet_weights(F, D, seed=0)
+    tr = sil.Trainer(sil.unet_config(F, D, B), list(wts.values()))
+    chips = torch.from_numpy(chips_h).cuda()
+    labs = torch.from_numpy(lab_h).cuda()
+    grads = torch.empty(tr.num_params, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    warm = max(3, args.warmup if args.warmup < 50 else 5)
+    losses = []
+    for _ in range(warm):
+        tr.step(chips, labs, lr=1e-4, grads=grads, loss=loss)
+        losses.append(float(loss.item()))
+    torch.cuda.synchronize()
+    steps = args.train_steps
+    clk = ClockSampler(0)
+    clk.start()
+    time.sleep(0.15)
+    t0 = time.monotonic()
+    dt = _time_cuda(lambda: tr.step(chips, labs, lr=1e-4, grads=grads, loss=loss, stream=st), steps, st)
+    t1 = time.monotonic()
+    clk.mark(t0, t1)
+    time.sleep(0.1)
+    clk.stop()
+    losses.append(float(loss.item()))
+    fwd = tr.net.flops_per_chip() * B
+    flops = 3 * fwd
+    achieved = flops / dt / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        peak, peak_src = float(pk["bf16_tflops_sustained"]), "measured bf16_tflops_sustained"
+        burst = float(pk["bf16_tflops"])
+    except Exception:
+        peak, peak_src, burst = 1700.0, "fallback (sustained)", 1900.0
+    host = torch.from_numpy(chips_h).pin_memory()
+    host_lab = torch.from_numpy(lab_h).pin_memory()
+    hloss = torch.empty(1, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.e2e_steps, steps))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        chips.copy_(host, non_blocking=True)
+        labs.copy_(host_lab, non_blocking=True)
+        tr.step(chips, labs, lr=1e-4, grads=grads, loss=loss)
+        hloss.copy_(loss, non_blocking=True)
+    torch.cuda.synchronize()
+    te = (time.perf_counter() - te0) / e2e_steps
+    errors = tr.net.error_count()
+    line = {
+        "metric": "U-Net training images/s (F=%d, depth %d, Adam, bf16 tensor cores)" % (F, D),
+        "value": B / dt, "unit": "images/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic chips of the seeded scene with the labeler's auto-labels, "
+                                 "seeded random initial weights",
+        "config": {"workload": f"U-Net training step, {B} chips of 256x256 per GPU, base width {F}, "
+                               f"depth {D} ({sil._lib.sil_unet_num_layers(D)} layers, "
+                               f"{tr.num_params} parameters)",
+                   "l2": "activations and their gradients (several GB per step) larger than L2"},
+        "e2e": {"value": B / te, "unit": "images/s",
+                "h2d_bytes_per_step": int(chips_h.nbytes + lab_h.nbytes), "d2h_bytes_per_step": 4},
+        "gpu_launches": int(steps * _train_launches(tr.shapes, D, F, B)),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "frac_of_burst": achieved / burst, "flops_per_step": flops,
+                     "flops_note": "3x the forward pass (forward, input gradients, weight gradients)"},
+        "loss": {"first": losses[0], "last": losses[-1]},
+        "clocks": clk.summary(),
+        "wait_errors": errors,
+        "paper_context": "585.88 images/s on one A100 (Table III; TensorFlow, its own U-Net widths)",
+    }
+    if not args.no_cpu_baseline:
+        import oracle.unet_train as T
+        import oracle.unet as U
+        n, t_c = 0, time.perf_counter()
+        w64 = {k: (U.bf16(w), b) for k, (w, b) in wts.items()}
+        while True:
+            x = U.prep(chips_h[n % B:n % B + 1])
+            acts, logits = T.forward_saved(x, w64, D)
+            T.backward_network(acts, logits, lab_h[n % B:n % B + 1], w64, D)
+            n += 1
+            if time.perf_counter() - t_c > args.cpu_budget:
+                break
+        tc = time.perf_counter() - t_c
+        line["cpu_baseline"] = {"value": n / tc, "unit": "images/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n} chips through the float64 numpy training oracle "
+                                          f"(forward + backward) in {tc:.1f} s"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -756,12 +892,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0,
                     help="oracle worker processes for the CPU baseline (0 = every host core)")
-    ap.add_argument("--config", default="scene", choices=["scene", "batch", "served", "sweep", "unet"],
-                    help="scene: the headline line; batch/served/sweep/unet: the other workloads")
+    ap.add_argument("--config", default="scene",
+                    choices=["scene", "batch", "served", "sweep", "unet", "train"],
+                    help="scene: the headline line; batch/served/sweep/unet/train: the other workloads")
     ap.add_argument("--unet-width", type=int, default=32)
     ap.add_argument("--unet-depth", type=int, default=5)
     ap.add_argument("--unet-batch", type=int, default=64)
     ap.add_argument("--unet-steps", type=int, default=50)
+    ap.add_argument("--train-batch", type=int, default=32)
+    ap.add_argument("--train-steps", type=int, default=20)
     ap.add_argument("--tiles", type=int, default=512)
     ap.add_argument("--rates", default="50,200,1000,2000")
     ap.add_argument("--served-seconds", type=float, default=60.0)
@@ -779,6 +918,8 @@ def main():
         return run_sweep(args)
     if args.config == "unet":
         return run_unet(args)
+    if args.config == "train":
+        return run_train(args)
     return run_sil(args)
 
 

@@ -145,6 +145,100 @@ sil_status sil_unet_tensor_shape(const sil_unet* net, int32_t i, int64_t dims[4]
  * buffers, so it is strided in place).  Asynchronous on `stream`. */
 sil_status sil_unet_copy_tensor(const sil_unet* net, int32_t i, void* dst, sil_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Training step (Sec. III-C "U-Net Model Training": the model is trained
+ * with the Adam optimizer on categorical cross-entropy; "Distributed U-Net
+ * Model Training using Horovod Framework": every worker computes the
+ * gradient of its own batch, the gradients are averaged across workers and
+ * each worker applies the same update).
+ *
+ * Readings where the paper is silent: the loss is the mean over the batch's
+ * pixels whose label is 0..2 (label 3, masked, is left out); the paper's
+ * dropout layers (rates and positions not given) are left out, so a step is
+ * deterministic up to float summation order; Adam takes TensorFlow's
+ * defaults b1 0.9, b2 0.999, eps 1e-7 (the learning rate is an argument); a
+ * 2x2 max pool passes its gradient to the first maximum of its window in the
+ * order (0,0), (0,1), (1,0), (1,1).
+ *
+ * Precision: the forward pass is sil_unet_forward's (bf16 weights and
+ * activations, f32 sums, f32 head); activation gradients are stored as
+ * bf16, parameter gradients, Adam moments and the master weights are f32.
+ * After each update the master weights are rounded to bf16 for the next
+ * forward and backward pass.
+ *
+ * Flat parameter vector: the layers in sil_unet_layer_shape order, each its
+ * weight (PyTorch layout) then its bias, f32 (offsets from
+ * sil_unet_trainer_param_offset); gradients use the same layout.
+ * ------------------------------------------------------------------------ */
+typedef struct sil_unet_trainer sil_unet_trainer;
+
+/* Creates a trainer and its network (the arguments of sil_unet_create; the
+ * host arrays become the initial master weights).  Besides the network's
+ * activations it allocates the activation gradients of max_batch chips, a
+ * <= 1 GiB buffer for the 3x3 layers' tap matrices and the f32 parameters
+ * and moments.  SIL_EINVAL, SIL_ENOMEM, SIL_ECUDA. */
+sil_status sil_unet_trainer_create(sil_unet_trainer** tr, const sil_unet_config* cfg,
+                                   const float* const* weights, const float* const* biases,
+                                   int32_t device);
+void sil_unet_trainer_destroy(sil_unet_trainer* tr);
+
+/* The trainer's network (owned by the trainer): its forward pass, tensor
+ * copies and error count are those of the current weights. */
+sil_unet* sil_unet_trainer_net(sil_unet_trainer* tr);
+
+/* Length of the flat parameter vector; -1 on NULL. */
+int64_t sil_unet_trainer_num_params(const sil_unet_trainer* tr);
+
+/* Offsets of layer i's weight and bias in the flat vector. */
+sil_status sil_unet_trainer_param_offset(const sil_unet_trainer* tr, int32_t i, int64_t* w_off,
+                                         int64_t* b_off);
+
+/* Forward pass, loss and gradient of n chips (1..max_batch): chips = DEVICE
+ * uint8 [n][256][256][3], labels = DEVICE uint8 [n][256][256] (0 thick ice,
+ * 1 thin ice, 2 open water, 3 left out).  Writes every element of grads
+ * (DEVICE f32 [num_params]) and the mean loss (DEVICE f32 scalar).
+ * Asynchronous on `stream`; the trainer's buffers are reused by the next
+ * call, so calls on one trainer must be ordered.  The weight gradients of
+ * the 3x3 and transposed convolutions are cuBLAS GEMMs (bf16 in, f32 out)
+ * over the batch's pixels; everything else runs in this library's kernels.
+ * Every reduction runs in a fixed order: the same weights and batch give
+ * the same gradient and loss bits on every call. */
+sil_status sil_unet_trainer_backward(sil_unet_trainer* tr, const uint8_t* chips,
+                                     const uint8_t* labels, int32_t n, float* grads, float* loss,
+                                     sil_stream stream);
+
+/* One Adam update of the master weights with grads (DEVICE f32
+ * [num_params], e.g. the average of every worker's sil_unet_trainer_backward
+ * output) at step t >= 1 with learning rate lr >= 0, then the network's
+ * weights are re-packed.  SIL_EINVAL on t < 1 or lr < 0. */
+sil_status sil_unet_trainer_adam(sil_unet_trainer* tr, const float* grads, float lr, int32_t t,
+                                 sil_stream stream);
+
+/* Copies the master weights to / from DEVICE f32 [num_params]; set also
+ * clears the Adam moments (a fresh optimizer) and re-packs the network
+ * (the broadcast of rank 0's initial weights). */
+sil_status sil_unet_trainer_get_params(const sil_unet_trainer* tr, float* dst, sil_stream stream);
+sil_status sil_unet_trainer_set_params(sil_unet_trainer* tr, const float* src, sil_stream stream);
+
+/* Stored activation gradients of the last backward pass. */
+typedef enum sil_unet_grad_kind {
+  SIL_UNET_GRAD_LAYER = 0, /* index = layer i (not the head): the gradient at
+                              its pre-activation (after the ReLU's mask); for
+                              a transposed convolution, at its output */
+  SIL_UNET_GRAD_CAT = 1,   /* index = level l: the gradient at the decoder's
+                              concatenation [upsampled, encoder output] */
+  SIL_UNET_GRAD_POOL = 2   /* index = level l: the gradient at level l's
+                              pooled output (before it meets the skip share) */
+} sil_unet_grad_kind;
+
+/* dims = {n, H, W, C} of that gradient; the copy writes DEVICE bf16 dense
+ * [n][H][W][C].  SIL_EINVAL on an unknown kind or index, or before the
+ * first backward pass. */
+sil_status sil_unet_trainer_grad_shape(const sil_unet_trainer* tr, int32_t kind, int32_t i,
+                                       int64_t dims[4]);
+sil_status sil_unet_trainer_copy_grad(const sil_unet_trainer* tr, int32_t kind, int32_t i,
+                                      void* dst, sil_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -146,6 +146,18 @@ _SIGS = {
     "sil_unet_set_fault": ([_P, _I32], _I32),
     "sil_unet_tensor_shape": ([_P, _I32, ctypes.POINTER(_I64)], _I32),
     "sil_unet_copy_tensor": ([_P, _I32, _P, _P], _I32),
+    "sil_unet_trainer_create": ([ctypes.POINTER(_P), _P, ctypes.POINTER(ctypes.POINTER(ctypes.c_float)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_float)), _I32], _I32),
+    "sil_unet_trainer_destroy": ([_P], None),
+    "sil_unet_trainer_net": ([_P], _P),
+    "sil_unet_trainer_num_params": ([_P], _I64),
+    "sil_unet_trainer_param_offset": ([_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], _I32),
+    "sil_unet_trainer_backward": ([_P, _P, _P, _I32, _P, _P, _P], _I32),
+    "sil_unet_trainer_adam": ([_P, _P, ctypes.c_float, _I32, _P], _I32),
+    "sil_unet_trainer_get_params": ([_P, _P, _P], _I32),
+    "sil_unet_trainer_set_params": ([_P, _P, _P], _I32),
+    "sil_unet_trainer_grad_shape": ([_P, _I32, _I32, ctypes.POINTER(_I64)], _I32),
+    "sil_unet_trainer_copy_grad": ([_P, _I32, _I32, _P, _P], _I32),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -539,34 +551,49 @@ def unet_layer_shapes(cfg: sil_unet_config):
     return out
 
 
+def _weight_arrays(cfg, weights):
+    """Host float32 arrays of (w, b) per layer, checked against the layer
+    shapes, as the C arrays of pointers sil_unet_create takes."""
+    shapes = unet_layer_shapes(cfg)
+    if len(weights) != len(shapes):
+        raise ValueError(f"{len(weights)} layers given, {len(shapes)} expected")
+    keep = []
+    W = (ctypes.POINTER(ctypes.c_float) * len(shapes))()
+    B = (ctypes.POINTER(ctypes.c_float) * len(shapes))()
+    for i, ((w, b), (shape, kind)) in enumerate(zip(weights, shapes)):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        if w.shape != shape:
+            raise ValueError(f"layer {i}: weight shape {w.shape}, expected {shape}")
+        keep += [w, b]
+        W[i] = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        B[i] = b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    return W, B, keep
+
+
 class UNet:
     """A network on the current CUDA device.  ``weights``: list of (w, b)
     float32 numpy arrays in the library's layer order (PyTorch layouts)."""
 
     def __init__(self, cfg: sil_unet_config, weights, device: int = 0):
-        shapes = unet_layer_shapes(cfg)
-        if len(weights) != len(shapes):
-            raise ValueError(f"{len(weights)} layers given, {len(shapes)} expected")
-        self._keep = []
-        W = (ctypes.POINTER(ctypes.c_float) * len(shapes))()
-        B = (ctypes.POINTER(ctypes.c_float) * len(shapes))()
-        for i, ((w, b), (shape, kind)) in enumerate(zip(weights, shapes)):
-            w = np.ascontiguousarray(w, dtype=np.float32)
-            b = np.ascontiguousarray(b, dtype=np.float32)
-            if w.shape != shape:
-                raise ValueError(f"layer {i}: weight shape {w.shape}, expected {shape}")
-            self._keep += [w, b]
-            W[i] = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
-            B[i] = b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        W, B, keep = _weight_arrays(cfg, weights)
         self.cfg = cfg
         self.handle = _P()
+        self._owner = None
         check(_lib.sil_unet_create(ctypes.byref(self.handle), ctypes.byref(cfg), W, B, int(device)))
-        self._keep = None
+        del keep
+
+    @classmethod
+    def _borrow(cls, handle, cfg, owner):
+        """The network of a Trainer (owned, and freed, by the trainer)."""
+        net = cls.__new__(cls)
+        net.cfg, net.handle, net._owner = cfg, _P(handle), owner
+        return net
 
     def __del__(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self, "_owner", None) is None:
             _lib.sil_unet_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def flops_per_chip(self) -> int:
         return int(_lib.sil_unet_flops_per_chip(ctypes.byref(self.cfg)))
@@ -615,3 +642,123 @@ class UNet:
         out = torch.empty(tuple(int(d) for d in dims), dtype=torch.bfloat16, device="cuda")
         check(_lib.sil_unet_copy_tensor(self.handle, int(i), out.data_ptr(), _stream_handle(stream)))
         return out
+
+
+# --------------------------------------------------------------------------
+# U-Net training step and data-parallel plumbing (include/sil_unet.h)
+# --------------------------------------------------------------------------
+UNET_GRAD_LAYER, UNET_GRAD_CAT, UNET_GRAD_POOL = 0, 1, 2
+
+
+class Trainer:
+    """Training of a U-Net on the current CUDA device: ``backward`` gives the
+    flat f32 gradient and the mean loss of a batch, ``adam`` applies one
+    update with a (possibly averaged) gradient.  ``net`` is the trained
+    network (forward pass, activations)."""
+
+    def __init__(self, cfg: sil_unet_config, weights, device: int = 0):
+        W, B, keep = _weight_arrays(cfg, weights)
+        self.cfg = cfg
+        self.handle = _P()
+        check(_lib.sil_unet_trainer_create(ctypes.byref(self.handle), ctypes.byref(cfg), W, B,
+                                           int(device)))
+        del keep
+        self.device = int(device)
+        self.num_params = int(_lib.sil_unet_trainer_num_params(self.handle))
+        self.net = UNet._borrow(_lib.sil_unet_trainer_net(self.handle), cfg, self)
+        self.shapes = unet_layer_shapes(cfg)
+        self.offsets = []
+        for i in range(len(self.shapes)):
+            wo, bo = _I64(), _I64()
+            check(_lib.sil_unet_trainer_param_offset(self.handle, i, ctypes.byref(wo), ctypes.byref(bo)))
+            self.offsets.append((int(wo.value), int(bo.value)))
+        self.t = 0
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.sil_unet_trainer_destroy(self.handle)
+            self.handle = None
+
+    def _flat(self):
+        import torch
+        return torch.empty(self.num_params, dtype=torch.float32, device=f"cuda:{self.device}")
+
+    def backward(self, chips, labels, grads=None, loss=None, stream=None):
+        """chips: cuda uint8 [n, 256, 256, 3]; labels: cuda uint8 [n, 256, 256]
+        (3: left out of the loss).  Returns (grads [num_params], loss [1])."""
+        import torch
+        grads = self._flat() if grads is None else grads
+        loss = torch.empty(1, dtype=torch.float32, device=grads.device) if loss is None else loss
+        check(_lib.sil_unet_trainer_backward(self.handle, chips.data_ptr(), labels.data_ptr(),
+                                             int(chips.shape[0]), grads.data_ptr(), loss.data_ptr(),
+                                             _stream_handle(stream)))
+        return grads, loss
+
+    def adam(self, grads, lr: float = 1e-3, t: int | None = None, stream=None) -> None:
+        """One Adam step (t: the step number, default one past the last)."""
+        self.t = self.t + 1 if t is None else int(t)
+        check(_lib.sil_unet_trainer_adam(self.handle, grads.data_ptr(), float(lr), self.t,
+                                         _stream_handle(stream)))
+
+    def params(self, stream=None):
+        out = self._flat()
+        check(_lib.sil_unet_trainer_get_params(self.handle, out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    def set_params(self, flat, stream=None) -> None:
+        """Loads the flat master weights (cuda float32 [num_params]) and starts
+        a fresh optimizer (moments zero, step count 0)."""
+        check(_lib.sil_unet_trainer_set_params(self.handle, flat.data_ptr(), _stream_handle(stream)))
+        self.t = 0
+
+    def unflatten(self, flat) -> list:
+        """[(w, b)] numpy float32 per layer from a flat vector."""
+        a = flat.detach().cpu().numpy() if hasattr(flat, "detach") else np.asarray(flat)
+        out = []
+        for (shape, kind), (wo, bo) in zip(self.shapes, self.offsets):
+            nw = int(np.prod(shape))
+            nb = shape[1] if kind == UNET_UP else shape[0]
+            out.append((a[wo:wo + nw].reshape(shape).copy(), a[bo:bo + nb].copy()))
+        return out
+
+    def grad_tensor(self, kind: int, i: int, stream=None):
+        """A stored activation gradient of the last backward pass (kind
+        UNET_GRAD_LAYER / CAT / POOL) as a cuda bfloat16 tensor [n, H, W, C]."""
+        import torch
+        dims = (_I64 * 4)()
+        check(_lib.sil_unet_trainer_grad_shape(self.handle, int(kind), int(i), dims))
+        out = torch.empty(tuple(int(d) for d in dims), dtype=torch.bfloat16, device=f"cuda:{self.device}")
+        check(_lib.sil_unet_trainer_copy_grad(self.handle, int(kind), int(i), out.data_ptr(),
+                                              _stream_handle(stream)))
+        return out
+
+    def step(self, chips, labels, lr: float = 1e-3, group=None, grads=None, loss=None, stream=None):
+        """One data-parallel step: local gradient, average over the process
+        group (none: this process alone), Adam.  Returns the local loss."""
+        grads, loss = self.backward(chips, labels, grads, loss, stream)
+        average_gradients_(grads, group)
+        self.adam(grads, lr, stream=stream)
+        return loss
+
+
+def average_gradients_(grads, group=None):
+    """In place: the mean of every rank's gradient (the all-reduce of the
+    data-parallel optimizer).  No-op without an initialised process group."""
+    import torch.distributed as dist
+    if group is None and not (dist.is_available() and dist.is_initialized()):
+        return grads
+    world = dist.get_world_size(group)
+    if world > 1:
+        dist.all_reduce(grads, op=dist.ReduceOp.SUM, group=group)
+        grads.div_(world)
+    return grads
+
+
+def broadcast_params_(trainer, src: int = 0, group=None):
+    """Every rank takes rank `src`'s weights and restarts its optimizer."""
+    import torch.distributed as dist
+    flat = trainer.params()
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.broadcast(flat, src=src, group=group)
+    trainer.set_params(flat)
+    return flat

@@ -24,7 +24,9 @@
 #include <cuda.h>  // CUtensorMap (the encoder is fetched at run time, no -lcuda)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cublas_v2.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -75,6 +77,10 @@ struct ConvArgs {
   unsigned int* err;       // count of bounded waits that ran out
   int tw;                  // tile width: 16 (8 rows x 16 pixels of one image) or
                            // 8 (the 8 x 8 pixels of two images; H = W = 8)
+  const __nv_bfloat16* mask;  // optional: output element kept only where this
+                              // tensor (same pixel and channel, stride ms) is > 0
+                              // (a ReLU's backward pass)
+  int64_t ms;
 };
 
 // A tile is 128 pixels.  Width 16: 8 image rows x 16 pixels of one image,
@@ -421,6 +427,13 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
           opix = (int64_t(b) * 2 * a.H + 2 * y + (sub >> 1)) * (2 * a.W) + 2 * x + (sub & 1);
         }
         uint32_t packed[8];
+        uint32_t mk[8];
+        if (a.mask && live) {
+          const uint4* mp = reinterpret_cast<const uint4*>(a.mask + opix * a.ms + co);
+          const uint4 m0 = mp[0], m1 = mp[1];
+          mk[0] = m0.x; mk[1] = m0.y; mk[2] = m0.z; mk[3] = m0.w;
+          mk[4] = m1.x; mk[5] = m1.y; mk[6] = m1.z; mk[7] = m1.w;
+        }
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           float f0 = __uint_as_float(v[2 * e]) + bias_s[co + 2 * e];
@@ -428,6 +441,12 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
           if (a.relu) {
             f0 = fmaxf(f0, 0.f);
             f1 = fmaxf(f1, 0.f);
+          }
+          if (a.mask) {
+            // bf16 x > 0 <=> its sign bit is clear and it is not zero
+            const uint32_t m = live ? mk[e] : 0u;
+            if ((m & 0x8000u) || (m & 0x7FFFu) == 0) f0 = 0.f;
+            if ((m & 0x80000000u) || (m & 0x7FFF0000u) == 0) f1 = 0.f;
           }
           const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
           packed[e] = *reinterpret_cast<const uint32_t*>(&h);
@@ -628,6 +647,7 @@ struct Layer {
   bool head = false;              // fused 1x1 head (last decoder conv)
   int tma = 0;                    // A tiles through a tensor map (see ConvArgs::tma)
   int tw = kTileW;                // tile width (see ConvArgs::tw)
+  Tensor mask;                    // ReLU mask of a backward layer (base null: none)
   CUtensorMap tmap{};             // 4-D map of the input: {Ci, W, H, max_batch}
 };
 
@@ -786,6 +806,8 @@ cudaError_t run_layer(const Layer& L, int n, unsigned int* err, const float* hea
   a.fault_it = (fault && L.tma) ? 0 : -1;
   a.err = err;
   a.tw = L.tw;
+  a.mask = L.mask.base;
+  a.ms = L.mask.stride;
   const int mtiles = (a.M + kBM - 1) / kBM, ntiles = L.N / L.NT;
   switch (L.NT) {
     case 16: return launch_conv_nt<16>(a, L.tmap, mtiles, ntiles, s);
@@ -1219,6 +1241,784 @@ extern "C" sil_status sil_unet_copy_tensor(const sil_unet* net, int32_t i, void*
                                           reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) {
     set_error("sil_unet_copy_tensor: %s", cudaGetErrorString(e));
+    return SIL_ECUDA;
+  }
+  return SIL_OK;
+}
+
+// ===========================================================================
+// Training step (Sec. III-C "U-Net Model Training": Adam, categorical
+// cross-entropy; "Distributed U-Net Model Training using Horovod
+// Framework": each worker's gradients are averaged before the update).
+//
+// Backward pass of a layer y = relu(conv(x) + b):
+//   dgrad  dx = conv(ds, w flipped), the same tcgen05 implicit-GEMM kernel
+//          as the forward with the weights rearranged (the output channels
+//          become the reduction, the spatial taps are mirrored); its
+//          epilogue applies the previous layer's ReLU mask, so it writes that
+//          layer's ds directly;
+//   wgrad  dw[co][tap, ci] = sum_p ds[p][co] x[p + tap][ci]: the taps of x
+//          gathered into one matrix (k_im2col), then a plain GEMM (cuBLAS,
+//          bf16 in, f32 out) over the batch's pixels; db = ds summed.
+// Transposed convolutions: the output gradient is regrouped per input pixel
+// (k_space_to_depth), after which dgrad is a 1x1 convolution and wgrad a
+// GEMM.  Pooling, the skip connections, the loss and the head have their own
+// small kernels.  Activations and activation gradients are bf16, parameter
+// gradients, Adam moments and master weights f32; after each update the
+// weights are re-packed on the device into the forward and dgrad layouts.
+// ===========================================================================
+namespace sil {
+namespace unet {
+
+constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-7f;
+
+__device__ __forceinline__ float bf2f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Pixels whose reference label is a class (0..2): the loss's denominator.
+__global__ void k_count_valid(const uint8_t* __restrict__ lab, int64_t P, unsigned int* count) {
+  unsigned int c = 0;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P;
+       p += int64_t(gridDim.x) * blockDim.x)
+    c += lab[p] < 3 ? 1u : 0u;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// Cross-entropy of the scores against the labels: each CTA's loss sum in
+// part[CTA] and dz = (softmax - onehot) / count, 0 for left-out pixels.
+__global__ void k_ce(const float* __restrict__ z, const uint8_t* __restrict__ lab, int64_t P,
+                     const unsigned int* __restrict__ count, float* __restrict__ dz,
+                     float* __restrict__ part) {
+  const float inv = 1.f / float(max(*count, 1u));
+  float acc = 0.f;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const int l = lab[p];
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    if (l < 3) {
+      const float z0 = z[3 * p], z1 = z[3 * p + 1], z2 = z[3 * p + 2];
+      const float m = fmaxf(z0, fmaxf(z1, z2));
+      const float e0 = expf(z0 - m), e1 = expf(z1 - m), e2 = expf(z2 - m);
+      const float se = e0 + e1 + e2;
+      const float zl = l == 0 ? z0 : (l == 1 ? z1 : z2);
+      acc += (m + logf(se) - zl);
+      d0 = (e0 / se - (l == 0 ? 1.f : 0.f)) * inv;
+      d1 = (e1 / se - (l == 1 ? 1.f : 0.f)) * inv;
+      d2 = (e2 / se - (l == 2 ? 1.f : 0.f)) * inv;
+    }
+    dz[3 * p] = d0;
+    dz[3 * p + 1] = d1;
+    dz[3 * p + 2] = d2;
+  }
+  // the CTA's loss sum, in a fixed order (k_sum_parts adds the CTAs')
+  __shared__ float wsum[32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += wsum[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// out[o] = sum over CTAs b (in order) of part[b width + o], divided by the
+// count of left-in pixels when `count` is given: the deterministic second
+// half of the loss and head-gradient reductions.
+__global__ void k_sum_parts(const float* __restrict__ part, int nparts, int width,
+                            const unsigned int* __restrict__ count, float* __restrict__ out) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < width; o += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int b = 0; b < nparts; ++b) acc += part[size_t(b) * width + o];
+    out[o] = count ? acc / float(max(*count, 1u)) : acc;
+  }
+}
+
+// Head (1x1, F -> 3): ds of the last decoder convolution = (dz . w) where
+// its output is > 0; gw[k][c] += sum_p dz[p][k] y[p][c], gb[k] += sum_p
+// dz[p][k].  A CTA stages 256 pixels at a time in shared memory; thread o
+// < 3 F + 3 keeps output o's partial sum over the CTA's chunks and stores
+// it in part[CTA][o] (k_sum_parts adds the CTAs' in order: the gradient is
+// the same bits on every run).
+__global__ void k_head_bwd(const float* __restrict__ dz, const __nv_bfloat16* __restrict__ y,
+                           int64_t ys, int F, int64_t P, const float* __restrict__ hw,
+                           __nv_bfloat16* __restrict__ ds, float* __restrict__ part) {
+  extern __shared__ float sh[];
+  float* sz = sh;              // [256][3]
+  float* sy = sh + 256 * 3;    // [256][F]
+  const int t = threadIdx.x;
+  float acc = 0.f;
+  const int o = t, k = o < 3 * F ? o / F : o - 3 * F, c = o < 3 * F ? o - k * F : 0;
+  for (int64_t p0 = int64_t(blockIdx.x) * 256; p0 < P; p0 += int64_t(gridDim.x) * 256) {
+    const int64_t p = p0 + t;
+    __syncthreads();
+    if (p < P) {
+      const float z0 = dz[3 * p], z1 = dz[3 * p + 1], z2 = dz[3 * p + 2];
+      sz[3 * t] = z0;
+      sz[3 * t + 1] = z1;
+      sz[3 * t + 2] = z2;
+      for (int j = 0; j < F; ++j) {
+        const float yv = bf2f(y[p * ys + j]);
+        sy[t * F + j] = yv;
+        const float g = z0 * hw[j] + z1 * hw[F + j] + z2 * hw[2 * F + j];
+        ds[p * F + j] = __float2bfloat16_rn(yv > 0.f ? g : 0.f);
+      }
+    } else {
+      sz[3 * t] = sz[3 * t + 1] = sz[3 * t + 2] = 0.f;
+      for (int j = 0; j < F; ++j) sy[t * F + j] = 0.f;
+    }
+    __syncthreads();
+    if (o < 3 * F)
+      for (int i = 0; i < 256; ++i) acc += sz[3 * i + k] * sy[i * F + c];
+    else if (o < 3 * F + 3)
+      for (int i = 0; i < 256; ++i) acc += sz[3 * i + k];
+  }
+  if (o < 3 * F + 3) part[size_t(blockIdx.x) * (3 * F + 3) + o] = acc;
+}
+
+// Gradient at an encoder level's output (before its 2x2 max pool): the pooled
+// gradient routed to the first maximum of each window plus the skip
+// connection's share, then that output's ReLU mask.  y: the output
+// (stride ys), gpool: [n][H/2][W/2][C], gskip: stride gss; ds dense.
+__global__ void k_pool_bwd(const __nv_bfloat16* __restrict__ y, int64_t ys,
+                           const __nv_bfloat16* __restrict__ gpool,
+                           const __nv_bfloat16* __restrict__ gskip, int64_t gss, int H, int W, int C,
+                           int64_t total, __nv_bfloat16* __restrict__ ds) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(i % C);
+    const int64_t pix = i / C;
+    const int x = int(pix % W), yy = int((pix / W) % H);
+    const int64_t b = pix / (int64_t(W) * H);
+    const int wy = yy & ~1, wx = x & ~1;
+    const int64_t base = (b * H + wy) * W + wx;
+    const float v00 = bf2f(y[base * ys + c]), v01 = bf2f(y[(base + 1) * ys + c]);
+    const float v10 = bf2f(y[(base + W) * ys + c]), v11 = bf2f(y[(base + W + 1) * ys + c]);
+    // first maximum in the order (0,0), (0,1), (1,0), (1,1)
+    int arg = 0;
+    float m = v00;
+    if (v01 > m) { m = v01; arg = 1; }
+    if (v10 > m) { m = v10; arg = 2; }
+    if (v11 > m) { m = v11; arg = 3; }
+    const int me = ((yy & 1) << 1) | (x & 1);
+    float g = bf2f(gskip[pix * gss + c]);
+    if (me == arg) g += bf2f(gpool[((b * (H / 2) + (yy >> 1)) * (W / 2) + (x >> 1)) * C + c]);
+    const float yv = bf2f(y[pix * ys + c]);
+    ds[pix * C + c] = __float2bfloat16_rn(yv > 0.f ? g : 0.f);
+  }
+}
+
+// Transposed convolution's output gradient regrouped per input pixel:
+// r[b][y][x][(2 i + j) C + c] = g[b][2 y + i][2 x + j][c] (g stride gs).
+__global__ void k_space_to_depth(const __nv_bfloat16* __restrict__ g, int64_t gs, int H, int W,
+                                 int C, int64_t total, __nv_bfloat16* __restrict__ r) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int k = int(i % (4 * C));
+    const int64_t pix = i / (4 * C);  // input pixel (H x W)
+    const int sub = k / C, c = k - sub * C;
+    const int x = int(pix % W), y = int((pix / W) % H);
+    const int64_t b = pix / (int64_t(W) * H);
+    const int64_t op = (b * 2 * H + 2 * y + (sub >> 1)) * (2 * W) + 2 * x + (sub & 1);
+    r[i] = g[op * gs + c];
+  }
+}
+
+// The 3x3 taps of x for pixels p0 .. p0 + np - 1 as one matrix:
+// col[p - p0][tap Cp + c] = x[p shifted by tap][c] (zero outside the image),
+// 8 channels (16 bytes) per thread.
+__global__ void k_im2col(const __nv_bfloat16* __restrict__ x, int64_t xs, int H, int W, int Cp,
+                         int64_t p0, int64_t np, __nv_bfloat16* __restrict__ col) {
+  const int chunks = Cp / 8;
+  const int64_t total = np * 9 * chunks;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int ch = int(i % chunks);
+    const int tap = int((i / chunks) % 9);
+    const int64_t pl = i / (int64_t(chunks) * 9), p = p0 + pl;
+    const int x0 = int(p % W), y0 = int((p / W) % H);
+    const int64_t b = p / (int64_t(W) * H);
+    const int yy = y0 + tap / 3 - 1, xx = x0 + tap % 3 - 1;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+      v = *reinterpret_cast<const uint4*>(x + ((b * H + yy) * W + xx) * xs + 8 * ch);
+    *reinterpret_cast<uint4*>(col + (pl * 9 + tap) * Cp + 8 * ch) = v;
+  }
+}
+
+// GEMM results -> the parameter gradient in PyTorch layout.
+//   conv:  raw[co + Co (tap Cp + ci)] -> gw[co][ci][tap]; gb[co] = rawb[co]
+//   up:    raw[ci + Ci (sub Co + co)] -> gw[ci][co][sub]; gb[co] = sum_sub rawb[sub Co + co]
+__global__ void k_wgrad_out(const float* __restrict__ raw, const float* __restrict__ rawb, int up,
+                            int Ci, int Co, int Cp, float* __restrict__ gw, float* __restrict__ gb) {
+  const int nw = up ? Ci * Co * 4 : Co * Ci * 9;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw + Co; i += gridDim.x * blockDim.x) {
+    if (i >= nw) {
+      const int co = i - nw;
+      gb[co] = up ? rawb[co] + rawb[Co + co] + rawb[2 * Co + co] + rawb[3 * Co + co] : rawb[co];
+      continue;
+    }
+    if (up) {
+      const int sub = i % 4, co = (i / 4) % Co, ci = i / (4 * Co);
+      gw[i] = raw[ci + size_t(Ci) * (sub * Co + co)];
+    } else {
+      const int tap = i % 9, ci = (i / 9) % Ci, co = i / (9 * Ci);
+      gw[i] = raw[co + size_t(Co) * (tap * Cp + ci)];
+    }
+  }
+}
+
+// One Adam step on the flat parameters: c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t).
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float c1, float c2) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const float gi = g[i];
+    const float mi = kAdamB1 * m[i] + (1.f - kAdamB1) * gi;
+    const float vi = kAdamB2 * v[i] + (1.f - kAdamB2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + kAdamEps);
+  }
+}
+
+__device__ __forceinline__ size_t sw128_off_d(int rr, int k) {
+  return size_t(rr >> 3) * 1024 + size_t(rr & 7) * 128 + size_t(((k >> 3) ^ (rr & 7)) << 4) +
+         size_t(k & 7) * 2;
+}
+
+// Weight blocks [N / NT][KT][NT x 64] (bf16, 128-byte swizzle) of a kernel
+// from the f32 PyTorch-layout weights w:
+//   mode 0 conv forward:  n = co, k = tap Cp + c        <- w[co][c][tap]
+//   mode 1 up forward:    n = sub Co + co, k = c        <- w[c][co][sub]
+//   mode 2 conv dgrad:    n = ci, k = tap Cop + co      <- w[co][ci][8 - tap]
+//   mode 3 up dgrad:      n = ci, k = sub Co + co       <- w[ci][co][sub]
+__global__ void k_pack(const float* __restrict__ w, int mode, int Ci, int Co, int Cp, int N, int NT,
+                       int KT, uint8_t* __restrict__ blk) {
+  const int64_t total = int64_t(N) * KT * kBK;
+  const size_t bsz = size_t(NT) * kBK * 2;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int n = int(i / (int64_t(KT) * kBK)), k = int(i % (int64_t(KT) * kBK));
+    float v = 0.f;
+    if (mode == 0) {
+      const int tap = k / Cp, c = k % Cp;
+      if (tap < 9 && c < Ci) v = w[(size_t(n) * Ci + c) * 9 + tap];
+    } else if (mode == 1) {
+      const int sub = n / Co, co = n % Co;
+      if (k < Ci) v = w[(size_t(k) * Co + co) * 4 + sub];
+    } else if (mode == 2) {
+      const int tap = k / Cp, co = k % Cp;  // Cp: the padded output channels of the forward
+      if (tap < 9 && co < Co && n < Ci) v = w[(size_t(co) * Ci + n) * 9 + (8 - tap)];
+    } else {
+      const int sub = k / Co, co = k % Co;
+      if (sub < 4 && n < Ci) v = w[(size_t(n) * Co + co) * 4 + sub];
+    }
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(blk + (size_t(n / NT) * KT + k / kBK) * bsz +
+                                      sw128_off_d(n % NT, k % kBK)) = b;
+  }
+}
+
+}  // namespace unet
+}  // namespace sil
+
+struct sil_unet_trainer {
+  sil_unet* net = nullptr;
+  int device = 0, D = 0, F = 0, B = 0, nl = 0;
+  std::vector<void*> allocs;
+  std::vector<int64_t> w_off, b_off;
+  int64_t nparams = 0;
+  float* p = nullptr;  // master weights, PyTorch layout, layer after layer (weight, bias)
+  float* m = nullptr;  // Adam moments
+  float* v = nullptr;
+  std::vector<sil::unet::Layer> bwd;    // dgrad launch of forward layer i (wblk null: none)
+  std::vector<sil::unet::Tensor> ds;    // gradient at layer i's pre-activation
+  std::vector<sil::unet::Tensor> gcat;  // per level: gradient of the concatenation
+  std::vector<sil::unet::Tensor> rr;    // per level: that gradient's first half, per input pixel
+  std::vector<sil::unet::Tensor> gpool; // per level: gradient at the pooled output
+  __nv_bfloat16* col = nullptr;
+  int64_t col_elems = 0;
+  float* raw = nullptr;
+  float* rawb = nullptr;
+  __nv_bfloat16* ones = nullptr;
+  float* logits = nullptr;
+  float* dz = nullptr;
+  unsigned int* count = nullptr;
+  float* zero_bias = nullptr;
+  float* part = nullptr;  // per-CTA partial sums of the loss and the head gradient
+  cublasHandle_t blas = nullptr;
+  int last_n = 0;
+};
+
+namespace {
+
+int enc_idx(int l, int j) { return 2 * l + j; }
+int bott_idx(int D, int j) { return 2 * D + j; }
+int up_idx(int D, int l) { return 2 * D + 2 + 3 * (D - 1 - l); }
+
+constexpr int kMaxGrid = 152 * 16;  // CTAs of the grid-stride kernels
+int grid_for(int64_t work, int threads) {
+  const int64_t g = (work + threads - 1) / threads;
+  return int(g < kMaxGrid ? (g > 0 ? g : 1) : kMaxGrid);
+}
+
+// out = sum over pixels of a^T b (column-major views, see the callers),
+// bf16 inputs, f32 output; beta 0 or 1.
+cublasStatus_t gemm_tn(cublasHandle_t h, int m, int n, int k, const void* A, int lda, const void* B,
+                       int ldb, float beta, float* C, int ldc, bool b_trans) {
+  const float one = 1.f;
+  return cublasGemmEx(h, CUBLAS_OP_N, b_trans ? CUBLAS_OP_T : CUBLAS_OP_N, m, n, k, &one, A,
+                      CUDA_R_16BF, lda, B, CUDA_R_16BF, ldb, &beta, C, CUDA_R_32F, ldc,
+                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+}
+
+// Rewrites the network's forward weight blocks, biases and head and the
+// dgrad blocks from the master weights.
+cudaError_t repack(sil_unet_trainer* tr, cudaStream_t s) {
+  sil_unet* net = tr->net;
+  for (int i = 0; i < tr->nl; ++i) {
+    const Layer& L = net->layers[i];
+    const float* w = tr->p + tr->w_off[i];
+    const float* b = tr->p + tr->b_off[i];
+    cudaError_t e;
+    if (L.kind == SIL_UNET_HEAD) {
+      e = cudaMemcpyAsync(net->head_w, w, sizeof(float) * kClasses * tr->F, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(net->head_b, b, sizeof(float) * kClasses, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    const bool up = L.kind == SIL_UNET_UP;
+    k_pack<<<grid_for(int64_t(L.N) * L.KT * kBK, 256), 256, 0, s>>>(w, up ? 1 : 0, L.ci, L.co,
+                                                                    L.cin_pad, L.N, L.NT, L.KT, L.wblk);
+    e = cudaMemcpyAsync(L.bias, b, sizeof(float) * L.co, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    const Layer& G = tr->bwd[i];
+    if (G.wblk)
+      k_pack<<<grid_for(int64_t(G.N) * G.KT * kBK, 256), 256, 0, s>>>(w, up ? 3 : 2, L.ci, L.co,
+                                                                      G.cin_pad, G.N, G.NT, G.KT, G.wblk);
+  }
+  return cudaGetLastError();
+}
+
+// wgrad of 3x3 layer i: raw = ds^T col (Co x 9 Cp), rawb = ds^T 1, in
+// pixel chunks that fit the im2col buffer; then the PyTorch layout.
+bool conv_wgrad(sil_unet_trainer* tr, int i, int n, float* grads, cudaStream_t s) {
+  const Layer& L = tr->net->layers[i];
+  const Tensor& x = L.in;
+  const Tensor& g = tr->ds[i];
+  const int Cp = L.cin_pad, K = 9 * Cp, Co = L.co;
+  const int64_t P = int64_t(n) * x.H * x.W;
+  const int64_t chunk = std::min<int64_t>(P, tr->col_elems / K);
+  bool ok = true;
+  for (int64_t p0 = 0; p0 < P && ok; p0 += chunk) {
+    const int64_t np = std::min(chunk, P - p0);
+    k_im2col<<<grid_for(np * 9 * (Cp / 8), 256), 256, 0, s>>>(x.base, x.stride, x.H, x.W, Cp, p0, np,
+                                                              tr->col);
+    const float beta = p0 ? 1.f : 0.f;
+    ok = gemm_tn(tr->blas, Co, K, int(np), g.base + p0 * Co, Co, tr->col, K, beta, tr->raw, Co, true) ==
+             CUBLAS_STATUS_SUCCESS &&
+         gemm_tn(tr->blas, Co, 1, int(np), g.base + p0 * Co, Co, tr->ones, int(np), beta, tr->rawb, Co,
+                 false) == CUBLAS_STATUS_SUCCESS;
+  }
+  k_wgrad_out<<<grid_for(int64_t(Co) * L.ci * 9 + Co, 256), 256, 0, s>>>(
+      tr->raw, tr->rawb, 0, L.ci, Co, Cp, grads + tr->w_off[i], grads + tr->b_off[i]);
+  return ok;
+}
+
+// wgrad of the transposed convolution of level l: raw = x^T r (Ci x 4 Co),
+// rawb = r^T 1 (4 Co).
+bool up_wgrad(sil_unet_trainer* tr, int l, int n, float* grads, cudaStream_t s) {
+  const int i = up_idx(tr->D, l);
+  const Layer& L = tr->net->layers[i];
+  const Tensor& x = L.in;
+  const Tensor& r = tr->rr[l];
+  const int64_t P = int64_t(n) * x.H * x.W;
+  const bool ok =
+      gemm_tn(tr->blas, L.ci, 4 * L.co, int(P), x.base, int(x.stride), r.base, 4 * L.co, 0.f, tr->raw,
+              L.ci, true) == CUBLAS_STATUS_SUCCESS &&
+      gemm_tn(tr->blas, 4 * L.co, 1, int(P), r.base, 4 * L.co, tr->ones, int(P), 0.f, tr->rawb,
+              4 * L.co, false) == CUBLAS_STATUS_SUCCESS;
+  k_wgrad_out<<<grid_for(int64_t(L.co) * L.ci * 4 + L.co, 256), 256, 0, s>>>(
+      tr->raw, tr->rawb, 1, L.ci, L.co, 0, grads + tr->w_off[i], grads + tr->b_off[i]);
+  return ok;
+}
+
+}  // namespace
+
+extern "C" void sil_unet_trainer_destroy(sil_unet_trainer* tr) {
+  if (!tr) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(tr->device);
+  if (tr->blas) cublasDestroy(tr->blas);
+  for (void* q : tr->allocs) cudaFree(q);
+  cudaSetDevice(prev);
+  sil_unet_destroy(tr->net);
+  delete tr;
+}
+
+extern "C" sil_status sil_unet_trainer_create(sil_unet_trainer** out, const sil_unet_config* cfg,
+                                              const float* const* weights,
+                                              const float* const* biases, int32_t device) {
+  if (!out) {
+    set_error("sil_unet_trainer_create: NULL");
+    return SIL_EINVAL;
+  }
+  *out = nullptr;
+  sil_unet* net = nullptr;
+  sil_status st = sil_unet_create(&net, cfg, weights, biases, device);
+  if (st != SIL_OK) return st;
+  sil_unet_trainer* tr = new (std::nothrow) sil_unet_trainer;
+  if (!tr) {
+    sil_unet_destroy(net);
+    return SIL_ENOMEM;
+  }
+  tr->net = net;
+  tr->device = device;
+  tr->D = cfg->depth;
+  tr->F = cfg->base_width;
+  tr->B = cfg->max_batch;
+  tr->nl = int(net->layers.size());
+  const int D = tr->D, B = tr->B;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  auto dalloc = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (st != SIL_OK) return nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+      set_error("sil_unet_trainer_create: cudaMalloc(%zu) failed", bytes);
+      st = SIL_ENOMEM;
+      return nullptr;
+    }
+    tr->allocs.push_back(q);
+    return q;
+  };
+  auto act = [&](int H, int C) {
+    Tensor t;
+    t.base = static_cast<__nv_bfloat16*>(dalloc(size_t(B) * H * H * C * 2));
+    t.stride = C;
+    t.H = t.W = H;
+    t.C = C;
+    return t;
+  };
+  // parameter offsets (sil_unet_layer_shape order, weight then bias)
+  int64_t raw_elems = 0, rawb_elems = 0, col_need = 0;
+  for (int i = 0; i < tr->nl; ++i) {
+    int64_t d[4];
+    int kind = 0;
+    layer_shape(*cfg, i, d, &kind);
+    tr->w_off.push_back(tr->nparams);
+    tr->nparams += d[0] * d[1] * d[2] * d[3];
+    tr->b_off.push_back(tr->nparams);
+    tr->nparams += kind == SIL_UNET_UP ? d[1] : d[0];
+    const Layer& L = net->layers[i];
+    if (kind == SIL_UNET_CONV3) {
+      raw_elems = std::max<int64_t>(raw_elems, int64_t(L.co) * 9 * L.cin_pad);
+      rawb_elems = std::max<int64_t>(rawb_elems, L.co);
+      col_need = std::max<int64_t>(col_need, int64_t(B) * L.in.H * L.in.W * 9 * L.cin_pad);
+    } else if (kind == SIL_UNET_UP) {
+      raw_elems = std::max<int64_t>(raw_elems, int64_t(L.ci) * 4 * L.co);
+      rawb_elems = std::max<int64_t>(rawb_elems, 4 * L.co);
+    }
+  }
+  tr->p = static_cast<float*>(dalloc(sizeof(float) * tr->nparams));
+  tr->m = static_cast<float*>(dalloc(sizeof(float) * tr->nparams));
+  tr->v = static_cast<float*>(dalloc(sizeof(float) * tr->nparams));
+  for (int i = 0; i < tr->nl && st == SIL_OK; ++i) {
+    const int64_t wl = tr->b_off[i] - tr->w_off[i];
+    const int64_t bl = (i + 1 < tr->nl ? tr->w_off[i + 1] : tr->nparams) - tr->b_off[i];
+    if (cudaMemcpy(tr->p + tr->w_off[i], weights[i], sizeof(float) * wl, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(tr->p + tr->b_off[i], biases[i], sizeof(float) * bl, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      st = SIL_ECUDA;
+  }
+  // the im2col buffer holds at most 1 GiB; larger layers go in pixel chunks
+  tr->col_elems = std::min<int64_t>(col_need, int64_t(1) << 29);
+  tr->col = static_cast<__nv_bfloat16*>(dalloc(size_t(tr->col_elems) * 2));
+  tr->raw = static_cast<float*>(dalloc(sizeof(float) * raw_elems));
+  tr->rawb = static_cast<float*>(dalloc(sizeof(float) * rawb_elems));
+  const int64_t P0 = int64_t(B) * kChip * kChip;
+  tr->ones = static_cast<__nv_bfloat16*>(dalloc(size_t(P0) * 2));
+  tr->logits = static_cast<float*>(dalloc(sizeof(float) * P0 * kClasses));
+  tr->dz = static_cast<float*>(dalloc(sizeof(float) * P0 * kClasses));
+  tr->count = static_cast<unsigned int*>(dalloc(sizeof(unsigned int)));
+  tr->zero_bias = static_cast<float*>(dalloc(sizeof(float) * kMaxCout));
+  tr->part = static_cast<float*>(dalloc(sizeof(float) * kMaxGrid * (kClasses * (tr->F + 1))));
+  if (st == SIL_OK) {
+    std::vector<uint16_t> one(size_t(P0), 0x3F80u);  // bfloat16 1.0
+    if (cudaMemcpy(tr->ones, one.data(), size_t(P0) * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(tr->zero_bias, 0, sizeof(float) * kMaxCout) != cudaSuccess ||
+        cudaMemset(tr->m, 0, sizeof(float) * tr->nparams) != cudaSuccess ||
+        cudaMemset(tr->v, 0, sizeof(float) * tr->nparams) != cudaSuccess)
+      st = SIL_ECUDA;
+  }
+  // activation gradients
+  tr->ds.resize(tr->nl);
+  tr->gcat.resize(D);
+  tr->rr.resize(D);
+  tr->gpool.resize(D);
+  for (int l = 0; l < D; ++l) {
+    const int H = kChip >> l, w = tr->F << l;
+    tr->gcat[l] = act(H, 2 * w);
+    tr->rr[l] = act(H / 2, 4 * w);
+    tr->gpool[l] = act(H / 2, w);
+  }
+  for (int i = 0; i < tr->nl; ++i) {
+    const Layer& L = net->layers[i];
+    if (L.kind == SIL_UNET_CONV3) {
+      tr->ds[i] = act(L.out.H, L.co);
+    } else if (L.kind == SIL_UNET_UP) {
+      const int l = D - 1 - (i - 2 * D - 2) / 3;
+      tr->ds[i] = tr->gcat[l];
+      tr->ds[i].C = L.co;
+    }
+  }
+  // dgrad launches: input = ds of the layer, output = the gradient at its
+  // input (masked by the producing layer's ReLU where there is one)
+  tr->bwd.resize(tr->nl);
+  auto dgrad = [&](int i, const Tensor& in, int taps, const Tensor& outt, const Tensor* mask) {
+    const Layer& L = net->layers[i];
+    Layer G;
+    G.kind = SIL_UNET_CONV3;
+    G.ci = in.C;
+    G.cin_pad = in.C;
+    G.co = L.ci;
+    G.N = L.ci;
+    G.NT = G.N < 128 ? G.N : 128;
+    G.taps = taps;
+    G.K = taps == 1 ? in.C : 9 * in.C;
+    G.KT = (G.K + kBK - 1) / kBK;
+    G.relu = false;
+    G.in = in;
+    G.out = outt;
+    if (mask) G.mask = *mask;
+    G.tma = (G.cin_pad % kBK == 0) ? 1 : (G.cin_pad == kBK / 2 && taps == 9) ? 2 : 0;
+    G.tw = in.W >= kTileW ? kTileW : 8;
+    G.bias = tr->zero_bias;
+    G.wblk = static_cast<uint8_t*>(dalloc(size_t(G.N) * G.KT * kBK * 2));
+    if (st == SIL_OK && G.tma && !encode_input_map(G, B)) G.tma = 0;
+    tr->bwd[i] = G;
+  };
+  for (int l = 0; l < D && st == SIL_OK; ++l) {
+    const int e0 = enc_idx(l, 0), e1 = enc_idx(l, 1), u = up_idx(D, l);
+    dgrad(e1, tr->ds[e1], 9, tr->ds[e0], &net->layers[e0].out);
+    if (l > 0) dgrad(e0, tr->ds[e0], 9, tr->gpool[l - 1], nullptr);
+    dgrad(u + 2, tr->ds[u + 2], 9, tr->ds[u + 1], &net->layers[u + 1].out);
+    dgrad(u + 1, tr->ds[u + 1], 9, tr->gcat[l], nullptr);
+    const int below = l == D - 1 ? bott_idx(D, 1) : up_idx(D, l + 1) + 2;
+    dgrad(u, tr->rr[l], 1, tr->ds[below], &net->layers[u].in);
+  }
+  if (st == SIL_OK) {
+    const int b0 = bott_idx(D, 0), b1 = bott_idx(D, 1);
+    dgrad(b1, tr->ds[b1], 9, tr->ds[b0], &net->layers[b0].out);
+    dgrad(b0, tr->ds[b0], 9, tr->gpool[D - 1], nullptr);
+  }
+  if (st == SIL_OK && cublasCreate(&tr->blas) != CUBLAS_STATUS_SUCCESS) {
+    set_error("sil_unet_trainer_create: cublasCreate failed");
+    st = SIL_ECUDA;
+  }
+  if (st == SIL_OK &&
+      cudaFuncSetAttribute(k_head_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(sizeof(float)) * 256 * (kClasses + 64)) != cudaSuccess)
+    st = SIL_ECUDA;
+  if (st == SIL_OK && (repack(tr, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)) {
+    set_error("sil_unet_trainer_create: weight packing failed");
+    st = SIL_ECUDA;
+  }
+  cudaSetDevice(prev);
+  if (st != SIL_OK) {
+    sil_unet_trainer_destroy(tr);
+    return st;
+  }
+  *out = tr;
+  return SIL_OK;
+}
+
+extern "C" sil_unet* sil_unet_trainer_net(sil_unet_trainer* tr) { return tr ? tr->net : nullptr; }
+
+extern "C" int64_t sil_unet_trainer_num_params(const sil_unet_trainer* tr) {
+  return tr ? tr->nparams : -1;
+}
+
+extern "C" sil_status sil_unet_trainer_param_offset(const sil_unet_trainer* tr, int32_t i,
+                                                    int64_t* w_off, int64_t* b_off) {
+  if (!tr || !w_off || !b_off || i < 0 || i >= tr->nl) {
+    set_error("sil_unet_trainer_param_offset: NULL or layer %d out of range", int(i));
+    return SIL_EINVAL;
+  }
+  *w_off = tr->w_off[i];
+  *b_off = tr->b_off[i];
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_trainer_backward(sil_unet_trainer* tr, const uint8_t* chips,
+                                                const uint8_t* labels, int32_t n, float* grads,
+                                                float* loss, sil_stream stream) {
+  if (!tr || !chips || !labels || !grads || !loss || n < 1 || n > tr->B) {
+    set_error("sil_unet_trainer_backward: NULL argument or n=%d outside 1..max_batch", int(n));
+    return SIL_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  sil_unet* net = tr->net;
+  const int D = tr->D, F = tr->F;
+  const int64_t P0 = int64_t(n) * kChip * kChip;
+  sil_status st = sil_unet_forward(net, chips, n, nullptr, tr->logits, stream);
+  if (st != SIL_OK) return st;
+  bool ok = cublasSetStream(tr->blas, s) == CUBLAS_STATUS_SUCCESS;
+  const int head = tr->nl - 1;
+  cudaError_t e = cudaMemsetAsync(tr->count, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess || !ok) {
+    set_error("sil_unet_trainer_backward: %s", ok ? cudaGetErrorString(e) : "cublasSetStream failed");
+    return SIL_ECUDA;
+  }
+  k_count_valid<<<grid_for(P0, 256), 256, 0, s>>>(labels, P0, tr->count);
+  const int gce = grid_for(P0, 256);
+  k_ce<<<gce, 256, 0, s>>>(tr->logits, labels, P0, tr->count, tr->dz, tr->part);
+  k_sum_parts<<<1, 32, 0, s>>>(tr->part, gce, 1, tr->count, loss);
+  {
+    // head: weight [3][F] then bias [3], contiguous in the flat gradient
+    const Layer& L = net->layers[up_idx(D, 0) + 2];
+    const int gh = grid_for(P0, 256 * 8), width = kClasses * (F + 1);
+    k_head_bwd<<<gh, 256, sizeof(float) * 256 * (kClasses + F), s>>>(
+        tr->dz, L.out.base, L.out.stride, F, P0, net->head_w, tr->ds[up_idx(D, 0) + 2].base, tr->part);
+    k_sum_parts<<<(width + 255) / 256, 256, 0, s>>>(tr->part, gh, width, nullptr,
+                                                    grads + tr->w_off[head]);
+  }
+  auto dgrad = [&](int i) {
+    if (e == cudaSuccess)
+      e = run_layer(tr->bwd[i], n, net->err, nullptr, nullptr, nullptr, nullptr, false, s);
+  };
+  for (int l = 0; l < D; ++l) {
+    const int u = up_idx(D, l), w = F << l;
+    ok = ok && conv_wgrad(tr, u + 2, n, grads, s);
+    dgrad(u + 2);
+    ok = ok && conv_wgrad(tr, u + 1, n, grads, s);
+    dgrad(u + 1);
+    const Tensor& g = tr->gcat[l];
+    const int h = g.H / 2;
+    const int64_t tot = int64_t(n) * h * h * 4 * w;
+    k_space_to_depth<<<grid_for(tot, 256), 256, 0, s>>>(g.base, g.stride, h, h, w, tot, tr->rr[l].base);
+    ok = ok && up_wgrad(tr, l, n, grads, s);
+    dgrad(u);
+  }
+  for (int j = 1; j >= 0; --j) {
+    ok = ok && conv_wgrad(tr, bott_idx(D, j), n, grads, s);
+    dgrad(bott_idx(D, j));
+  }
+  for (int l = D - 1; l >= 0; --l) {
+    const int e0 = enc_idx(l, 0), e1 = enc_idx(l, 1), w = F << l;
+    const Layer& L = net->layers[e1];
+    const int64_t tot = int64_t(n) * L.out.H * L.out.W * w;
+    k_pool_bwd<<<grid_for(tot, 256), 256, 0, s>>>(L.out.base, L.out.stride, tr->gpool[l].base,
+                                                  tr->gcat[l].base + w, tr->gcat[l].stride, L.out.H,
+                                                  L.out.W, w, tot, tr->ds[e1].base);
+    ok = ok && conv_wgrad(tr, e1, n, grads, s);
+    dgrad(e1);
+    ok = ok && conv_wgrad(tr, e0, n, grads, s);
+    if (l > 0) dgrad(e0);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess || !ok) {
+    set_error("sil_unet_trainer_backward: %s", ok ? cudaGetErrorString(e) : "cuBLAS GEMM failed");
+    return SIL_ECUDA;
+  }
+  tr->last_n = n;
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_trainer_adam(sil_unet_trainer* tr, const float* grads, float lr,
+                                            int32_t t, sil_stream stream) {
+  if (!tr || !grads || t < 1 || !(lr >= 0.f)) {
+    set_error("sil_unet_trainer_adam: NULL, step t=%d < 1 or negative learning rate", int(t));
+    return SIL_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const float c1 = float(1.0 / (1.0 - std::pow(double(kAdamB1), t)));
+  const float c2 = float(1.0 / (1.0 - std::pow(double(kAdamB2), t)));
+  k_adam<<<grid_for(tr->nparams, 256), 256, 0, s>>>(tr->p, grads, tr->m, tr->v, tr->nparams, lr, c1, c2);
+  const cudaError_t e = repack(tr, s);
+  if (e != cudaSuccess) {
+    set_error("sil_unet_trainer_adam: %s", cudaGetErrorString(e));
+    return SIL_ECUDA;
+  }
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_trainer_get_params(const sil_unet_trainer* tr, float* dst,
+                                                  sil_stream stream) {
+  if (!tr || !dst) {
+    set_error("sil_unet_trainer_get_params: NULL");
+    return SIL_EINVAL;
+  }
+  if (cudaMemcpyAsync(dst, tr->p, sizeof(float) * tr->nparams, cudaMemcpyDeviceToDevice,
+                      reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    set_error("sil_unet_trainer_get_params: copy failed");
+    return SIL_ECUDA;
+  }
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_trainer_set_params(sil_unet_trainer* tr, const float* src,
+                                                  sil_stream stream) {
+  if (!tr || !src) {
+    set_error("sil_unet_trainer_set_params: NULL");
+    return SIL_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(tr->p, src, sizeof(float) * tr->nparams, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tr->m, 0, sizeof(float) * tr->nparams, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tr->v, 0, sizeof(float) * tr->nparams, s);
+  if (e == cudaSuccess) e = repack(tr, s);
+  if (e != cudaSuccess) {
+    set_error("sil_unet_trainer_set_params: %s", cudaGetErrorString(e));
+    return SIL_ECUDA;
+  }
+  return SIL_OK;
+}
+
+namespace {
+// The stored gradient of kind k (sil_unet_grad_kind) and index i.
+bool grad_of(const sil_unet_trainer* tr, int k, int i, Tensor* t) {
+  if (!tr) return false;
+  if (k == SIL_UNET_GRAD_LAYER && i >= 0 && i < tr->nl - 1) *t = tr->ds[i];
+  else if (k == SIL_UNET_GRAD_CAT && i >= 0 && i < tr->D) *t = tr->gcat[i];
+  else if (k == SIL_UNET_GRAD_POOL && i >= 0 && i < tr->D) *t = tr->gpool[i];
+  else return false;
+  return true;
+}
+}  // namespace
+
+extern "C" sil_status sil_unet_trainer_grad_shape(const sil_unet_trainer* tr, int32_t kind,
+                                                  int32_t i, int64_t dims[4]) {
+  Tensor t;
+  if (!dims || !grad_of(tr, kind, i, &t)) {
+    set_error("sil_unet_trainer_grad_shape: NULL or no stored gradient of kind %d, index %d",
+              int(kind), int(i));
+    return SIL_EINVAL;
+  }
+  dims[0] = tr->last_n;
+  dims[1] = t.H;
+  dims[2] = t.W;
+  dims[3] = t.C;
+  return SIL_OK;
+}
+
+extern "C" sil_status sil_unet_trainer_copy_grad(const sil_unet_trainer* tr, int32_t kind,
+                                                 int32_t i, void* dst, sil_stream stream) {
+  Tensor t;
+  if (!dst || !grad_of(tr, kind, i, &t) || tr->last_n < 1) {
+    set_error("sil_unet_trainer_copy_grad: NULL, no backward pass yet, or no stored gradient of "
+              "kind %d, index %d", int(kind), int(i));
+    return SIL_EINVAL;
+  }
+  const size_t rows = size_t(tr->last_n) * t.H * t.W;
+  if (cudaMemcpy2DAsync(dst, size_t(t.C) * 2, t.base, size_t(t.stride) * 2, size_t(t.C) * 2, rows,
+                        cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    set_error("sil_unet_trainer_copy_grad: copy failed");
     return SIL_ECUDA;
   }
   return SIL_OK;
