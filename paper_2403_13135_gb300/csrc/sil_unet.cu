@@ -1322,52 +1322,84 @@ __global__ void k_ce(const float* __restrict__ z, const uint8_t* __restrict__ la
   }
 }
 
-// out[o] = sum over CTAs b (in order) of part[b width + o], divided by the
-// count of left-in pixels when `count` is given: the deterministic second
-// half of the loss and head-gradient reductions.
+// out[o] = sum over CTAs b of part[b width + o], divided by the count of
+// left-in pixels when `count` is given: the second half of the loss and
+// head-gradient reductions.  One CTA per output: thread t adds parts t,
+// t + 256, ..., then a tree in shared memory; the order is fixed, so the
+// result is the same bits on every run.
 __global__ void k_sum_parts(const float* __restrict__ part, int nparts, int width,
                             const unsigned int* __restrict__ count, float* __restrict__ out) {
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < width; o += gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    for (int b = 0; b < nparts; ++b) acc += part[size_t(b) * width + o];
-    out[o] = count ? acc / float(max(*count, 1u)) : acc;
+  __shared__ float red[256];
+  const int o = blockIdx.x, t = threadIdx.x;
+  float acc = 0.f;
+  for (int b = t; b < nparts; b += 256) acc += part[size_t(b) * width + o];
+  red[t] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) red[t] += red[t + h];
+    __syncthreads();
   }
+  if (t == 0) out[o] = count ? red[0] / float(max(*count, 1u)) : red[0];
+}
+
+__device__ __forceinline__ void unpack8(const uint4 v, float* f) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[e]));
+    f[2 * e] = t.x;
+    f[2 * e + 1] = t.y;
+  }
+}
+__device__ __forceinline__ uint4 pack8(const float* f) {
+  uint32_t w[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+    w[e] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // Head (1x1, F -> 3): ds of the last decoder convolution = (dz . w) where
-// its output is > 0; gw[k][c] += sum_p dz[p][k] y[p][c], gb[k] += sum_p
-// dz[p][k].  A CTA stages 256 pixels at a time in shared memory; thread o
-// < 3 F + 3 keeps output o's partial sum over the CTA's chunks and stores
-// it in part[CTA][o] (k_sum_parts adds the CTAs' in order: the gradient is
-// the same bits on every run).
+// its output is > 0; gw[k][c] = sum_p dz[p][k] y[p][c], gb[k] = sum_p
+// dz[p][k].  A CTA stages 256 pixels at a time in shared memory (16-byte
+// loads of the activation, 8 channels each); thread o < 3 F + 3 keeps
+// output o's partial sum over the CTA's chunks and stores it in
+// part[CTA][o] (k_sum_parts adds the CTAs').
 __global__ void k_head_bwd(const float* __restrict__ dz, const __nv_bfloat16* __restrict__ y,
                            int64_t ys, int F, int64_t P, const float* __restrict__ hw,
                            __nv_bfloat16* __restrict__ ds, float* __restrict__ part) {
   extern __shared__ float sh[];
   float* sz = sh;              // [256][3]
   float* sy = sh + 256 * 3;    // [256][F]
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, chunks = F / 8;
   float acc = 0.f;
   const int o = t, k = o < 3 * F ? o / F : o - 3 * F, c = o < 3 * F ? o - k * F : 0;
   for (int64_t p0 = int64_t(blockIdx.x) * 256; p0 < P; p0 += int64_t(gridDim.x) * 256) {
-    const int64_t p = p0 + t;
     __syncthreads();
-    if (p < P) {
-      const float z0 = dz[3 * p], z1 = dz[3 * p + 1], z2 = dz[3 * p + 2];
-      sz[3 * t] = z0;
-      sz[3 * t + 1] = z1;
-      sz[3 * t + 2] = z2;
-      for (int j = 0; j < F; ++j) {
-        const float yv = bf2f(y[p * ys + j]);
-        sy[t * F + j] = yv;
-        const float g = z0 * hw[j] + z1 * hw[F + j] + z2 * hw[2 * F + j];
-        ds[p * F + j] = __float2bfloat16_rn(yv > 0.f ? g : 0.f);
-      }
-    } else {
-      sz[3 * t] = sz[3 * t + 1] = sz[3 * t + 2] = 0.f;
-      for (int j = 0; j < F; ++j) sy[t * F + j] = 0.f;
+    for (int q = t; q < 256 * 3; q += 256) sz[q] = p0 + q / 3 < P ? dz[3 * p0 + q] : 0.f;
+    for (int q = t; q < 256 * chunks; q += 256) {
+      const int pl = q / chunks, ch = q - pl * chunks;
+      const int64_t p = p0 + pl;
+      const uint4 v = p < P ? *reinterpret_cast<const uint4*>(y + p * ys + 8 * ch) : make_uint4(0, 0, 0, 0);
+      unpack8(v, sy + pl * F + 8 * ch);
     }
     __syncthreads();
+    for (int q = t; q < 256 * chunks; q += 256) {
+      const int pl = q / chunks, ch = q - pl * chunks;
+      const int64_t p = p0 + pl;
+      if (p >= P) continue;
+      float g[8];
+      const float z0 = sz[3 * pl], z1 = sz[3 * pl + 1], z2 = sz[3 * pl + 2];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int j = 8 * ch + e;
+        const float v = z0 * hw[j] + z1 * hw[F + j] + z2 * hw[2 * F + j];
+        g[e] = sy[pl * F + j] > 0.f ? v : 0.f;
+      }
+      *reinterpret_cast<uint4*>(ds + p * F + 8 * ch) = pack8(g);
+    }
     if (o < 3 * F)
       for (int i = 0; i < 256; ++i) acc += sz[3 * i + k] * sy[i * F + c];
     else if (o < 3 * F + 3)
@@ -1377,77 +1409,100 @@ __global__ void k_head_bwd(const float* __restrict__ dz, const __nv_bfloat16* __
 }
 
 // Gradient at an encoder level's output (before its 2x2 max pool): the pooled
-// gradient routed to the first maximum of each window plus the skip
-// connection's share, then that output's ReLU mask.  y: the output
-// (stride ys), gpool: [n][H/2][W/2][C], gskip: stride gss; ds dense.
+// gradient routed to the first maximum of each window (order (0,0), (0,1),
+// (1,0), (1,1)) plus the skip connection's share, then that output's ReLU
+// mask.  y: the output (stride ys), gpool: [n][H/2][W/2][C], gskip: stride
+// gss; ds dense.  One thread per window and 8 channels: every input is read
+// once, 16 bytes at a time.
 __global__ void k_pool_bwd(const __nv_bfloat16* __restrict__ y, int64_t ys,
                            const __nv_bfloat16* __restrict__ gpool,
                            const __nv_bfloat16* __restrict__ gskip, int64_t gss, int H, int W, int C,
-                           int64_t total, __nv_bfloat16* __restrict__ ds) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+                           int64_t windows, __nv_bfloat16* __restrict__ ds) {
+  const int chunks = C / 8, Wh = W / 2, Hh = H / 2;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < windows * chunks;
        i += int64_t(gridDim.x) * blockDim.x) {
-    const int c = int(i % C);
-    const int64_t pix = i / C;
-    const int x = int(pix % W), yy = int((pix / W) % H);
-    const int64_t b = pix / (int64_t(W) * H);
-    const int wy = yy & ~1, wx = x & ~1;
-    const int64_t base = (b * H + wy) * W + wx;
-    const float v00 = bf2f(y[base * ys + c]), v01 = bf2f(y[(base + 1) * ys + c]);
-    const float v10 = bf2f(y[(base + W) * ys + c]), v11 = bf2f(y[(base + W + 1) * ys + c]);
-    // first maximum in the order (0,0), (0,1), (1,0), (1,1)
-    int arg = 0;
-    float m = v00;
-    if (v01 > m) { m = v01; arg = 1; }
-    if (v10 > m) { m = v10; arg = 2; }
-    if (v11 > m) { m = v11; arg = 3; }
-    const int me = ((yy & 1) << 1) | (x & 1);
-    float g = bf2f(gskip[pix * gss + c]);
-    if (me == arg) g += bf2f(gpool[((b * (H / 2) + (yy >> 1)) * (W / 2) + (x >> 1)) * C + c]);
-    const float yv = bf2f(y[pix * ys + c]);
-    ds[pix * C + c] = __float2bfloat16_rn(yv > 0.f ? g : 0.f);
+    const int ch = int(i % chunks);
+    const int64_t win = i / chunks;
+    const int wx = int(win % Wh), wy = int((win / Wh) % Hh);
+    const int64_t b = win / (int64_t(Wh) * Hh);
+    const int64_t p0 = (b * H + 2 * wy) * W + 2 * wx;
+    const int64_t pix[4] = {p0, p0 + 1, p0 + W, p0 + W + 1};
+    float yv[4][8], sk[4][8], gp[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      unpack8(*reinterpret_cast<const uint4*>(y + pix[q] * ys + 8 * ch), yv[q]);
+      unpack8(*reinterpret_cast<const uint4*>(gskip + pix[q] * gss + 8 * ch), sk[q]);
+    }
+    unpack8(*reinterpret_cast<const uint4*>(gpool + win * C + 8 * ch), gp);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      int arg = 0;
+      float m = yv[0][e];
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (yv[q][e] > m) {
+          m = yv[q][e];
+          arg = q;
+        }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float g = sk[q][e] + (q == arg ? gp[e] : 0.f);
+        sk[q][e] = yv[q][e] > 0.f ? g : 0.f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(ds + pix[q] * C + 8 * ch) = pack8(sk[q]);
   }
 }
 
 // Transposed convolution's output gradient regrouped per input pixel:
-// r[b][y][x][(2 i + j) C + c] = g[b][2 y + i][2 x + j][c] (g stride gs).
+// r[b][y][x][(2 i + j) C + c] = g[b][2 y + i][2 x + j][c] (g stride gs),
+// 8 channels (16 bytes) per thread.
 __global__ void k_space_to_depth(const __nv_bfloat16* __restrict__ g, int64_t gs, int H, int W,
                                  int C, int64_t total, __nv_bfloat16* __restrict__ r) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const int k = int(i % (4 * C));
-    const int64_t pix = i / (4 * C);  // input pixel (H x W)
-    const int sub = k / C, c = k - sub * C;
-    const int x = int(pix % W), y = int((pix / W) % H);
-    const int64_t b = pix / (int64_t(W) * H);
-    const int64_t op = (b * 2 * H + 2 * y + (sub >> 1)) * (2 * W) + 2 * x + (sub & 1);
-    r[i] = g[op * gs + c];
-  }
-}
-
-// The 3x3 taps of x for pixels p0 .. p0 + np - 1 as one matrix:
-// col[p - p0][tap Cp + c] = x[p shifted by tap][c] (zero outside the image),
-// 8 channels (16 bytes) per thread.
-__global__ void k_im2col(const __nv_bfloat16* __restrict__ x, int64_t xs, int H, int W, int Cp,
-                         int64_t p0, int64_t np, __nv_bfloat16* __restrict__ col) {
-  const int chunks = Cp / 8;
-  const int64_t total = np * 9 * chunks;
+  const int chunks = C / 8;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
        i += int64_t(gridDim.x) * blockDim.x) {
     const int ch = int(i % chunks);
-    const int tap = int((i / chunks) % 9);
-    const int64_t pl = i / (int64_t(chunks) * 9), p = p0 + pl;
-    const int x0 = int(p % W), y0 = int((p / W) % H);
-    const int64_t b = p / (int64_t(W) * H);
-    const int yy = y0 + tap / 3 - 1, xx = x0 + tap % 3 - 1;
+    const int64_t rest = i / chunks;
+    const int sub = int(rest & 3);
+    const int64_t pix = rest >> 2;  // input pixel (H x W)
+    const int x = int(pix % W), yy = int((pix / W) % H);
+    const int64_t b = pix / (int64_t(W) * H);
+    const int64_t op = (b * 2 * H + 2 * yy + (sub >> 1)) * (2 * W) + 2 * x + (sub & 1);
+    *reinterpret_cast<uint4*>(r + pix * 4 * C + sub * C + 8 * ch) =
+        *reinterpret_cast<const uint4*>(g + op * gs + 8 * ch);
+  }
+}
+
+// The 3x3 taps of x for pixels p0 .. p0 + np - 1 as one matrix with a
+// leading column of ones (its product with ds is the bias gradient):
+// row p - p0 = [1, 0 x 7, x[p shifted by tap 0][0 .. Cp), ..., tap 8], zero
+// outside the image; ld = 9 Cp + 8.  8 channels (16 bytes) per thread; H, W
+// and Cp / 8 are powers of two (shifts and masks, no divisions but by 9).
+__global__ void k_im2col(const __nv_bfloat16* __restrict__ x, int64_t xs, int hlog, int wlog,
+                         int clog, int64_t p0, int np, __nv_bfloat16* __restrict__ col) {
+  const int Cp = 8 << clog, ld = 9 * Cp + 8;
+  const uint32_t total = uint32_t(np) * 9u << clog;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const uint32_t ch = i & ((1u << clog) - 1u), q = i >> clog;
+    const uint32_t pl = q / 9u, tap = q - 9u * pl;
+    const int64_t p = p0 + pl;
+    const int x0 = int(p & ((1 << wlog) - 1)), y0 = int((p >> wlog) & ((1 << hlog) - 1));
+    const int64_t b = p >> (wlog + hlog);
+    const int yy = y0 + int(tap) / 3 - 1, xx = x0 + int(tap) % 3 - 1;
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-      v = *reinterpret_cast<const uint4*>(x + ((b * H + yy) * W + xx) * xs + 8 * ch);
-    *reinterpret_cast<uint4*>(col + (pl * 9 + tap) * Cp + 8 * ch) = v;
+    if (yy >= 0 && yy < (1 << hlog) && xx >= 0 && xx < (1 << wlog))
+      v = *reinterpret_cast<const uint4*>(x + ((((b << hlog) + yy) << wlog) + xx) * xs + 8 * ch);
+    __nv_bfloat16* row = col + int64_t(pl) * ld;
+    *reinterpret_cast<uint4*>(row + 8 + tap * Cp + 8 * ch) = v;
+    if (tap == 0 && ch == 0) *reinterpret_cast<uint4*>(row) = make_uint4(0x3F80u, 0, 0, 0);  // bf16 1.0
   }
 }
 
 // GEMM results -> the parameter gradient in PyTorch layout.
-//   conv:  raw[co + Co (tap Cp + ci)] -> gw[co][ci][tap]; gb[co] = rawb[co]
+//   conv:  raw[co + Co (8 + tap Cp + ci)] -> gw[co][ci][tap]; gb[co] = raw[co]
+//          (rawb unused)
 //   up:    raw[ci + Ci (sub Co + co)] -> gw[ci][co][sub]; gb[co] = sum_sub rawb[sub Co + co]
 __global__ void k_wgrad_out(const float* __restrict__ raw, const float* __restrict__ rawb, int up,
                             int Ci, int Co, int Cp, float* __restrict__ gw, float* __restrict__ gb) {
@@ -1455,7 +1510,7 @@ __global__ void k_wgrad_out(const float* __restrict__ raw, const float* __restri
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw + Co; i += gridDim.x * blockDim.x) {
     if (i >= nw) {
       const int co = i - nw;
-      gb[co] = up ? rawb[co] + rawb[Co + co] + rawb[2 * Co + co] + rawb[3 * Co + co] : rawb[co];
+      gb[co] = up ? rawb[co] + rawb[Co + co] + rawb[2 * Co + co] + rawb[3 * Co + co] : raw[co];
       continue;
     }
     if (up) {
@@ -1463,7 +1518,7 @@ __global__ void k_wgrad_out(const float* __restrict__ raw, const float* __restri
       gw[i] = raw[ci + size_t(Ci) * (sub * Co + co)];
     } else {
       const int tap = i % 9, ci = (i / 9) % Ci, co = i / (9 * Ci);
-      gw[i] = raw[co + size_t(Co) * (tap * Cp + ci)];
+      gw[i] = raw[co + size_t(Co) * (8 + tap * Cp + ci)];
     }
   }
 }
@@ -1495,28 +1550,37 @@ __device__ __forceinline__ size_t sw128_off_d(int rr, int k) {
 //   mode 3 up dgrad:      n = ci, k = sub Co + co       <- w[ci][co][sub]
 __global__ void k_pack(const float* __restrict__ w, int mode, int Ci, int Co, int Cp, int N, int NT,
                        int KT, uint8_t* __restrict__ blk) {
-  const int64_t total = int64_t(N) * KT * kBK;
+  // one thread per row n and 8 consecutive k (one 16-byte chunk of a
+  // swizzled 128-byte row); Cp and Co are multiples of 8, so the 8 k share
+  // their tap / sub-position
+  const int64_t total = int64_t(N) * KT * (kBK / 8);
   const size_t bsz = size_t(NT) * kBK * 2;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
        i += int64_t(gridDim.x) * blockDim.x) {
-    const int n = int(i / (int64_t(KT) * kBK)), k = int(i % (int64_t(KT) * kBK));
-    float v = 0.f;
-    if (mode == 0) {
-      const int tap = k / Cp, c = k % Cp;
-      if (tap < 9 && c < Ci) v = w[(size_t(n) * Ci + c) * 9 + tap];
-    } else if (mode == 1) {
-      const int sub = n / Co, co = n % Co;
-      if (k < Ci) v = w[(size_t(k) * Co + co) * 4 + sub];
-    } else if (mode == 2) {
-      const int tap = k / Cp, co = k % Cp;  // Cp: the padded output channels of the forward
-      if (tap < 9 && co < Co && n < Ci) v = w[(size_t(co) * Ci + n) * 9 + (8 - tap)];
-    } else {
-      const int sub = k / Co, co = k % Co;
-      if (sub < 4 && n < Ci) v = w[(size_t(n) * Co + co) * 4 + sub];
+    const int n = int(i / (int64_t(KT) * (kBK / 8)));
+    const int k0 = int(i % (int64_t(KT) * (kBK / 8))) * 8;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + e;
+      float u = 0.f;
+      if (mode == 0) {
+        const int tap = k / Cp, c = k % Cp;
+        if (tap < 9 && c < Ci) u = w[(size_t(n) * Ci + c) * 9 + tap];
+      } else if (mode == 1) {
+        const int sub = n / Co, co = n % Co;
+        if (k < Ci) u = w[(size_t(k) * Co + co) * 4 + sub];
+      } else if (mode == 2) {
+        const int tap = k / Cp, co = k % Cp;  // Cp: the padded output channels of the forward
+        if (tap < 9 && co < Co && n < Ci) u = w[(size_t(co) * Ci + n) * 9 + (8 - tap)];
+      } else {
+        const int sub = k / Co, co = k % Co;
+        if (sub < 4 && n < Ci) u = w[(size_t(n) * Co + co) * 4 + sub];
+      }
+      v[e] = u;
     }
-    const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    *reinterpret_cast<__nv_bfloat16*>(blk + (size_t(n / NT) * KT + k / kBK) * bsz +
-                                      sw128_off_d(n % NT, k % kBK)) = b;
+    const int rr = n % NT, kk = k0 % kBK;
+    *reinterpret_cast<uint4*>(blk + (size_t(n / NT) * KT + k0 / kBK) * bsz + sw128_off_d(rr, kk)) = pack8(v);
   }
 }
 
@@ -1590,40 +1654,38 @@ cudaError_t repack(sil_unet_trainer* tr, cudaStream_t s) {
       continue;
     }
     const bool up = L.kind == SIL_UNET_UP;
-    k_pack<<<grid_for(int64_t(L.N) * L.KT * kBK, 256), 256, 0, s>>>(w, up ? 1 : 0, L.ci, L.co,
+    k_pack<<<grid_for(int64_t(L.N) * L.KT * (kBK / 8), 256), 256, 0, s>>>(w, up ? 1 : 0, L.ci, L.co,
                                                                     L.cin_pad, L.N, L.NT, L.KT, L.wblk);
     e = cudaMemcpyAsync(L.bias, b, sizeof(float) * L.co, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     const Layer& G = tr->bwd[i];
     if (G.wblk)
-      k_pack<<<grid_for(int64_t(G.N) * G.KT * kBK, 256), 256, 0, s>>>(w, up ? 3 : 2, L.ci, L.co,
+      k_pack<<<grid_for(int64_t(G.N) * G.KT * (kBK / 8), 256), 256, 0, s>>>(w, up ? 3 : 2, L.ci, L.co,
                                                                       G.cin_pad, G.N, G.NT, G.KT, G.wblk);
   }
   return cudaGetLastError();
 }
 
-// wgrad of 3x3 layer i: raw = ds^T col (Co x 9 Cp), rawb = ds^T 1, in
-// pixel chunks that fit the im2col buffer; then the PyTorch layout.
+// wgrad of 3x3 layer i: raw = ds^T [1 | col] (Co x (8 + 9 Cp); column 0 is
+// the bias gradient), in pixel chunks that fit the im2col buffer; then the
+// PyTorch layout.
 bool conv_wgrad(sil_unet_trainer* tr, int i, int n, float* grads, cudaStream_t s) {
   const Layer& L = tr->net->layers[i];
   const Tensor& x = L.in;
   const Tensor& g = tr->ds[i];
-  const int Cp = L.cin_pad, K = 9 * Cp, Co = L.co;
+  const int Cp = L.cin_pad, ld = 9 * Cp + 8, Co = L.co;
   const int64_t P = int64_t(n) * x.H * x.W;
-  const int64_t chunk = std::min<int64_t>(P, tr->col_elems / K);
+  const int64_t chunk = std::min<int64_t>(P, tr->col_elems / ld);
   bool ok = true;
   for (int64_t p0 = 0; p0 < P && ok; p0 += chunk) {
     const int64_t np = std::min(chunk, P - p0);
-    k_im2col<<<grid_for(np * 9 * (Cp / 8), 256), 256, 0, s>>>(x.base, x.stride, x.H, x.W, Cp, p0, np,
-                                                              tr->col);
-    const float beta = p0 ? 1.f : 0.f;
-    ok = gemm_tn(tr->blas, Co, K, int(np), g.base + p0 * Co, Co, tr->col, K, beta, tr->raw, Co, true) ==
-             CUBLAS_STATUS_SUCCESS &&
-         gemm_tn(tr->blas, Co, 1, int(np), g.base + p0 * Co, Co, tr->ones, int(np), beta, tr->rawb, Co,
-                 false) == CUBLAS_STATUS_SUCCESS;
+    k_im2col<<<grid_for(np * 9 * (Cp / 8), 256), 256, 0, s>>>(x.base, x.stride, ilog2(x.H), ilog2(x.W),
+                                                              ilog2(Cp / 8), p0, int(np), tr->col);
+    ok = gemm_tn(tr->blas, Co, ld, int(np), g.base + p0 * Co, Co, tr->col, ld, p0 ? 1.f : 0.f,
+                 tr->raw, Co, true) == CUBLAS_STATUS_SUCCESS;
   }
   k_wgrad_out<<<grid_for(int64_t(Co) * L.ci * 9 + Co, 256), 256, 0, s>>>(
-      tr->raw, tr->rawb, 0, L.ci, Co, Cp, grads + tr->w_off[i], grads + tr->b_off[i]);
+      tr->raw, nullptr, 0, L.ci, Co, Cp, grads + tr->w_off[i], grads + tr->b_off[i]);
   return ok;
 }
 
@@ -1716,9 +1778,8 @@ extern "C" sil_status sil_unet_trainer_create(sil_unet_trainer** out, const sil_
     tr->nparams += kind == SIL_UNET_UP ? d[1] : d[0];
     const Layer& L = net->layers[i];
     if (kind == SIL_UNET_CONV3) {
-      raw_elems = std::max<int64_t>(raw_elems, int64_t(L.co) * 9 * L.cin_pad);
-      rawb_elems = std::max<int64_t>(rawb_elems, L.co);
-      col_need = std::max<int64_t>(col_need, int64_t(B) * L.in.H * L.in.W * 9 * L.cin_pad);
+      raw_elems = std::max<int64_t>(raw_elems, int64_t(L.co) * (9 * L.cin_pad + 8));
+      col_need = std::max<int64_t>(col_need, int64_t(B) * L.in.H * L.in.W * (9 * L.cin_pad + 8));
     } else if (kind == SIL_UNET_UP) {
       raw_elems = std::max<int64_t>(raw_elems, int64_t(L.ci) * 4 * L.co);
       rawb_elems = std::max<int64_t>(rawb_elems, 4 * L.co);
@@ -1878,15 +1939,14 @@ extern "C" sil_status sil_unet_trainer_backward(sil_unet_trainer* tr, const uint
   k_count_valid<<<grid_for(P0, 256), 256, 0, s>>>(labels, P0, tr->count);
   const int gce = grid_for(P0, 256);
   k_ce<<<gce, 256, 0, s>>>(tr->logits, labels, P0, tr->count, tr->dz, tr->part);
-  k_sum_parts<<<1, 32, 0, s>>>(tr->part, gce, 1, tr->count, loss);
+  k_sum_parts<<<1, 256, 0, s>>>(tr->part, gce, 1, tr->count, loss);
   {
     // head: weight [3][F] then bias [3], contiguous in the flat gradient
     const Layer& L = net->layers[up_idx(D, 0) + 2];
     const int gh = grid_for(P0, 256 * 8), width = kClasses * (F + 1);
     k_head_bwd<<<gh, 256, sizeof(float) * 256 * (kClasses + F), s>>>(
         tr->dz, L.out.base, L.out.stride, F, P0, net->head_w, tr->ds[up_idx(D, 0) + 2].base, tr->part);
-    k_sum_parts<<<(width + 255) / 256, 256, 0, s>>>(tr->part, gh, width, nullptr,
-                                                    grads + tr->w_off[head]);
+    k_sum_parts<<<width, 256, 0, s>>>(tr->part, gh, width, nullptr, grads + tr->w_off[head]);
   }
   auto dgrad = [&](int i) {
     if (e == cudaSuccess)
@@ -1900,7 +1960,7 @@ extern "C" sil_status sil_unet_trainer_backward(sil_unet_trainer* tr, const uint
     dgrad(u + 1);
     const Tensor& g = tr->gcat[l];
     const int h = g.H / 2;
-    const int64_t tot = int64_t(n) * h * h * 4 * w;
+    const int64_t tot = int64_t(n) * h * h * 4 * (w / 8);
     k_space_to_depth<<<grid_for(tot, 256), 256, 0, s>>>(g.base, g.stride, h, h, w, tot, tr->rr[l].base);
     ok = ok && up_wgrad(tr, l, n, grads, s);
     dgrad(u);
@@ -1912,10 +1972,10 @@ extern "C" sil_status sil_unet_trainer_backward(sil_unet_trainer* tr, const uint
   for (int l = D - 1; l >= 0; --l) {
     const int e0 = enc_idx(l, 0), e1 = enc_idx(l, 1), w = F << l;
     const Layer& L = net->layers[e1];
-    const int64_t tot = int64_t(n) * L.out.H * L.out.W * w;
-    k_pool_bwd<<<grid_for(tot, 256), 256, 0, s>>>(L.out.base, L.out.stride, tr->gpool[l].base,
-                                                  tr->gcat[l].base + w, tr->gcat[l].stride, L.out.H,
-                                                  L.out.W, w, tot, tr->ds[e1].base);
+    const int64_t windows = int64_t(n) * (L.out.H / 2) * (L.out.W / 2);
+    k_pool_bwd<<<grid_for(windows * (w / 8), 256), 256, 0, s>>>(
+        L.out.base, L.out.stride, tr->gpool[l].base, tr->gcat[l].base + w, tr->gcat[l].stride, L.out.H,
+        L.out.W, w, windows, tr->ds[e1].base);
     ok = ok && conv_wgrad(tr, e1, n, grads, s);
     dgrad(e1);
     ok = ok && conv_wgrad(tr, e0, n, grads, s);
