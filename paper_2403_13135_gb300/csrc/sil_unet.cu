@@ -89,6 +89,8 @@ struct ConvArgs {
 // 8 x 8 maps of the fifth level): the whole 8 x 8 images 2 mt and 2 mt + 1,
 // tile row r is pixel (r % 64 / 8, r % 8) of image 2 mt + r / 64.
 constexpr int kTileW = 16, kTileH = 8;
+// pixel tiles per work unit of the tensor-map layers (1 or 2, see ConvCfg)
+constexpr int kUnitTiles = 2;
 __device__ __forceinline__ void tile_origin(int mt, int H, int W, int tw, int& b, int& y0, int& x0) {
   if (tw == 8) {
     b = 2 * mt;
@@ -101,6 +103,33 @@ __device__ __forceinline__ void tile_origin(int mt, int H, int W, int tw, int& b
   y0 = ty * kTileH;
   x0 = (rem - ty * tx) * kTileW;
 }
+// Work units of MT tiles that share a stage's weight block: for width 16,
+// MT vertically stacked 8 x 16 tiles of one image (tile j at rows y0 + 8 j);
+// for width 8, the 2 MT images 2 MT u .. (tile j: images b + 2 j, + 1).
+// MT = 1 is tile_origin.
+template <int MT>
+__device__ __forceinline__ void unit_origin(int u, int H, int W, int tw, int& b, int& y0, int& x0) {
+  if (MT == 1) {
+    tile_origin(u, H, W, tw, b, y0, x0);
+    return;
+  }
+  if (tw == 8) {
+    b = 2 * MT * u;
+    y0 = x0 = 0;
+    return;
+  }
+  const int tx = W / kTileW, per_img = (H / (kTileH * MT)) * tx;
+  b = u / per_img;
+  const int rem = u - b * per_img, ty = rem / tx;
+  y0 = ty * kTileH * MT;
+  x0 = (rem - ty * tx) * kTileW;
+}
+// Origin of tile j of a unit.
+__device__ __forceinline__ void sub_origin(int j, int tw, int& b, int& y0) {
+  if (tw == 8) b += 2 * j;
+  else y0 += kTileH * j;
+}
+
 // Image and pixel of tile row r.
 __device__ __forceinline__ void tile_pixel(int r, int tw, int b0, int y0, int x0, int& b, int& y,
                                            int& x) {
@@ -170,46 +199,55 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
          (uint64_t(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-template <int NT>
+template <int NT, int MT = 1>
 struct ConvCfg {
-  // Narrow tiles (NT <= 32) run three CTAs per SM with three stages each:
-  // their per-stage time is set by the single producer and MMA threads'
-  // instruction latencies (a stage is only 64 tensor-pipe cycles of work),
-  // so more independent CTAs per SM beat a deeper ring; wider tiles run two.
-  static constexpr int kMinBlocks = NT <= 32 ? 3 : 2;
-  static constexpr int kStages = NT >= 128 ? 3 : (NT <= 32 ? 3 : 4);
-  static constexpr int kA = kBM * kBK * 2;
+  // MT = 1: narrow tiles (NT <= 32) run three CTAs per SM with three stages
+  // each: their per-stage time is set by the single producer and MMA
+  // threads' instruction latencies (a stage is only 64 tensor-pipe cycles of
+  // work), so more independent CTAs per SM beat a deeper ring; wider tiles
+  // run two.  MT = 2: a stage holds two pixel tiles (one 16-row box per tap)
+  // that share the weight block, halving the box issues and the weight
+  // traffic per pixel; two CTAs per SM.
+  static constexpr int kMinBlocks = MT == 2 ? 2 : (NT <= 32 ? 3 : 2);
+  static constexpr int kStages = MT == 2 ? (NT <= 32 ? 3 : 2) : (NT >= 128 ? 3 : (NT <= 32 ? 3 : 4));
+  static constexpr int kA = MT * kBM * kBK * 2;
   static constexpr int kB = NT * kBK * 2;
   static constexpr int kStage = kA + kB;
   static constexpr int kSmem = kStages * kStage + 1024;  // + alignment slack
-  // two accumulators of NT float32 columns (the epilogue of one tile runs
-  // while the next tile accumulates)
-  static constexpr int kTmemCols = 2 * NT < 32 ? 32 : 2 * NT;
+  static constexpr int kSmemMax = kSmem + kMaxCout * 4;  // + the biases
+  // accumulators of MT x NT float32 columns: two (the epilogue of one unit
+  // runs while the next accumulates) when they fit in half the tensor
+  // memory, else one (the SM's other CTA overlaps instead)
+  static constexpr int kAccBufs = 2 * MT * NT <= 256 ? 2 : 1;
+  static constexpr int kTmemCols = kAccBufs * MT * NT < 32 ? 32 : kAccBufs * MT * NT;
   // kind::f16 instruction descriptor: D f32, A and B bf16, both K-major,
   // N >> 3 at bit 17, M >> 4 at bit 24.
   static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                      (uint32_t(NT >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
 };
 
-// Persistent: CTA b handles tiles b, b + gridDim.x, ... (tile t = M tile
-// t / ntiles, N tile t % ntiles).  Warps 0-3 produce A/B stages, warps 4-7
-// drain the accumulators, warp 8 issues the MMAs.
-template <int NT>
-__global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
+// Persistent: CTA b handles work items b, b + gridDim.x, ... (item t = M
+// unit t / ntiles of MT pixel tiles, N tile t % ntiles).  Warps 0-3 produce
+// A/B stages, warps 4-7 drain the accumulators, warp 8 issues the MMAs.
+template <int NT, int MT>
+__global__ void __launch_bounds__(kConvThreads, (ConvCfg<NT, MT>::kMinBlocks))
     k_conv(const ConvArgs a, const __grid_constant__ CUtensorMap tmap, int ntiles, int ntotal) {
-  using C = ConvCfg<NT>;
+  using C = ConvCfg<NT, MT>;
+  constexpr int NB = C::kAccBufs;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], acc_full[NB], acc_empty[NB];
   __shared__ uint32_t tmem_slot;
   __shared__ int failed_s;
-  __shared__ float bias_s[kMaxCout];
   __shared__ float head_s[kClasses * 64 + kClasses];
   volatile int* failed = &failed_s;
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
+  // the layer's biases after the ring (the launch adds cout floats to the
+  // dynamic shared memory)
+  float* bias_s = reinterpret_cast<float*>(smem + S * C::kStage);
   for (int i = tid; i < a.cout; i += kConvThreads) bias_s[i] = a.bias[i];
+
   if (a.head_w)
     for (int i = tid; i < kClasses * (a.cout + 1); i += kConvThreads)
       head_s[i] = i < kClasses * a.cout ? a.head_w[i] : a.head_b[i - kClasses * a.cout];
@@ -218,7 +256,7 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
       mbar_init(smem_u32(&full_bar[s]), a.tma ? 2 : kProducers + 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
       mbar_init(smem_u32(&acc_empty[b]), kEpilogue);
     }
@@ -251,7 +289,7 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
       for (int t = blockIdx.x; t < ntotal && ok; t += gridDim.x) {
         const int mt = t / ntiles, nt = t - mt * ntiles;
         int b, y0, x0;
-        tile_origin(mt, a.H, a.W, a.tw, b, y0, x0);
+        unit_origin<MT>(mt, a.H, a.W, a.tw, b, y0, x0);
         for (int kt = 0; kt < a.KT; ++kt, ++it) {
           const int s = it % S;
           if (it >= S && !mbar_wait(smem_u32(&empty_bar[s]), uint32_t((it / S - 1) & 1), failed)) {
@@ -274,7 +312,8 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
           }
           // mode 1: one box, tap k0 / Ci, channels k0 % Ci .. + 63; mode 2:
           // taps 2 kt and 2 kt + 1, all 32 channels each (a tap past the
-          // ninth is a box far outside the image: zeros)
+          // ninth is a box far outside the image: zeros); a box covers the
+          // unit's MT tiles (8 MT rows, or 2 MT images of 8 x 8)
           // (the test hook leaves one stage's boxes out: its wait runs out)
           const int nbox = it == a.fault_it ? 0 : (a.tma == 2 ? 2 : 1);
           for (int bx = 0; bx < nbox; ++bx) {
@@ -286,7 +325,7 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
               tap = a.taps == 1 ? 4 : (k0 >> a.cin_log2);
               c0 = a.taps == 1 ? k0 : (k0 & cmask);
             }
-            const int yy = tap < 9 ? y0 + tap / 3 - 1 : -4 * kTileH;
+            const int yy = tap < 9 ? y0 + tap / 3 - 1 : -4 * kTileH * MT;
             asm volatile(
                 "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
                     a_s + uint32_t(bx * (C::kA / 2))),
@@ -303,8 +342,10 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
         }
     }
   } else if (warp < 4) {
-    // ---- producers, gather path: rows 32 warp + 4 i + lane / 8, 16-byte
-    // chunk lane % 8
+    // ---- producers, gather path (one tile per unit; the host gives units
+    // of two tiles only to tensor-map layers): rows 32 warp + 4 i + lane /
+    // 8, 16-byte chunk lane % 8
+    if constexpr (MT == 1) {
     const int j = lane & 7;
     uint32_t soff[8];
 #pragma unroll
@@ -388,29 +429,34 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
         ok = false;
       }
     asm volatile("cp.async.wait_all;" ::: "memory");
+    }
   } else if (warp < 8) {
     // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31
     const int q = warp & 3, r = 32 * q + lane;
     int tl = 0;
+    const int nimg = a.M / (a.H * a.W);
     for (int t = blockIdx.x; t < ntotal; t += gridDim.x, ++tl) {
-      const int mt = t / ntiles, nt = t - mt * ntiles, buf = tl & 1;
-      if (!mbar_wait(smem_u32(&acc_full[buf]), uint32_t((tl >> 1) & 1), failed)) {
+      const int mt = t / ntiles, nt = t - mt * ntiles, buf = tl % NB;
+      if (!mbar_wait(smem_u32(&acc_full[buf]), uint32_t((tl / NB) & 1), failed)) {
         if (lane == 0) give_up(failed, a.err);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int p = mt * kBM + r;
-      int b0, y0, x0, b, y, x;
-      tile_origin(mt, a.H, a.W, a.tw, b0, y0, x0);
+      int ub, uy0, ux0;
+      unit_origin<MT>(mt, a.H, a.W, a.tw, ub, uy0, ux0);
+#pragma unroll 1
+      for (int j = 0; j < MT; ++j) {
+      int b0 = ub, y0 = uy0, x0 = ux0, b, y, x;
+      sub_origin(j, a.tw, b0, y0);
       tile_pixel(r, a.tw, b0, y0, x0, b, y, x);
-      const bool live = p < a.M;
+      const bool live = b < nimg;
       float hacc[kClasses];
 #pragma unroll
       for (int k = 0; k < kClasses; ++k) hacc[k] = a.head_w ? head_s[kClasses * a.cout + k] : 0.f;
 #pragma unroll 1
       for (int c0 = 0; c0 < NT; c0 += 16) {
         uint32_t v[16];
-        const uint32_t ta = tmem + (uint32_t(32 * q) << 16) + uint32_t(buf * NT + c0);
+        const uint32_t ta = tmem + (uint32_t(32 * q) << 16) + uint32_t((buf * MT + j) * NT + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
@@ -508,7 +554,8 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
         }
         if (a.labels) a.labels[op] = uint8_t(best);
       }
-      // this accumulator may be overwritten by the tile after next
+      }  // tile j of the unit
+      // this accumulator may be overwritten by the unit after next
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
     }
@@ -517,13 +564,13 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
     int it = 0, tl = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntotal && ok; t += gridDim.x, ++tl) {
-      const int buf = tl & 1;
-      if (tl >= 2 && !mbar_wait(smem_u32(&acc_empty[buf]), uint32_t(((tl >> 1) - 1) & 1), failed)) {
+      const int buf = tl % NB;
+      if (tl >= NB && !mbar_wait(smem_u32(&acc_empty[buf]), uint32_t(((tl / NB) - 1) & 1), failed)) {
         give_up(failed, a.err);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t d = tmem + uint32_t(buf * NT);
+      const uint32_t d = tmem + uint32_t(buf * MT * NT);
       for (int kt = 0; kt < a.KT; ++kt, ++it) {
         const int s = it % S;
         if (!mbar_wait(smem_u32(&full_bar[s]), uint32_t((it / S) & 1), failed)) {
@@ -537,17 +584,22 @@ __global__ void __launch_bounds__(kConvThreads, ConvCfg<NT>::kMinBlocks)
         const uint32_t a0 = smem_u32(smem + s * C::kStage), b0 = a0 + uint32_t(C::kA);
 #pragma unroll
         for (int kk = 0; kk < kBK / 16; ++kk) {
-          // A: 128-byte rows (one box or the per-row gather), or with two
-          // 32-channel boxes, box kk / 2 at 32 bytes per K slice
-          const uint64_t ad = a.tma == 2 ? sw64_desc(a0 + uint32_t((kk >> 1) * (C::kA / 2) + 32 * (kk & 1)))
-                                         : sw128_desc(a0 + 32 * kk);
           const uint64_t bd = sw128_desc(b0 + 32 * kk);
           const uint32_t acc = (kt | kk) ? 1u : 0u;
-          asm volatile(
-              "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
-                  d),
-              "l"(ad), "l"(bd), "r"(C::kIdesc), "r"(acc)
-              : "memory");
+#pragma unroll
+          for (int j = 0; j < MT; ++j) {
+            // A of tile j: 128-byte rows (one box or the per-row gather),
+            // tile j 128 rows further; with two 32-channel boxes, box kk / 2
+            // at 32 bytes per K slice, tile j 128 64-byte rows further
+            const uint64_t ad =
+                a.tma == 2 ? sw64_desc(a0 + uint32_t((kk >> 1) * (C::kA / 2) + j * (kBM * 64) + 32 * (kk & 1)))
+                           : sw128_desc(a0 + uint32_t(j * (kBM * 128) + 32 * kk));
+            asm volatile(
+                "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                    d + uint32_t(j * NT)),
+                "l"(ad), "l"(bd), "r"(C::kIdesc), "r"(acc)
+                : "memory");
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&empty_bar[s]))
@@ -647,6 +699,7 @@ struct Layer {
   bool head = false;              // fused 1x1 head (last decoder conv)
   int tma = 0;                    // A tiles through a tensor map (see ConvArgs::tma)
   int tw = kTileW;                // tile width (see ConvArgs::tw)
+  int mt = 1;                     // pixel tiles per work unit (see ConvCfg)
   Tensor mask;                    // ReLU mask of a backward layer (base null: none)
   CUtensorMap tmap{};             // 4-D map of the input: {Ci, W, H, max_batch}
 };
@@ -732,9 +785,11 @@ bool encode_input_map(Layer& L, int batch) {
   const cuuint64_t es = 2;
   const cuuint64_t strides[3] = {cuuint64_t(L.in.stride) * es, cuuint64_t(L.in.W) * L.in.stride * es,
                                  cuuint64_t(L.in.H) * L.in.W * L.in.stride * es};
-  // a tile of width 16: 16 x 8 pixels of one image; of width 8: two 8 x 8 images
+  // a tile of width 16: 16 x 8 pixels of one image; of width 8: two 8 x 8
+  // images; a box covers the work unit's mt tiles
   const cuuint32_t box[4] = {cuuint32_t(L.tma == 2 ? kBK / 2 : kBK), cuuint32_t(L.tw),
-                             cuuint32_t(kTileH), cuuint32_t(L.tw == 8 ? 2 : 1)};
+                             cuuint32_t(L.tw == 8 ? kTileH : kTileH * L.mt),
+                             cuuint32_t(L.tw == 8 ? 2 * L.mt : 1)};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return enc(&L.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, L.in.base, dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -742,14 +797,14 @@ bool encode_input_map(Layer& L, int batch) {
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NT>
+template <int NT, int MT>
 cudaError_t launch_conv_nt(const ConvArgs& a, const CUtensorMap& tmap, int mtiles, int ntiles,
                            cudaStream_t s) {
   static int ctas_per_sm = 0;  // per process; set before the first launch
   static int sms = 0;
   if (!ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         ConvCfg<NT>::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_conv<NT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         ConvCfg<NT, MT>::kSmemMax);
     int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
     cudaFuncAttributes fa{};
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -757,16 +812,17 @@ cudaError_t launch_conv_nt(const ConvArgs& a, const CUtensorMap& tmap, int mtile
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conv<NT>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conv<NT, MT>);
     if (e != cudaSuccess) return e;
     // The occupancy calculator reports one CTA per SM for any kernel that
     // allocates tensor memory, so the resident count is derived from the
     // kernel's own shared memory, registers and tensor-memory columns (an
     // SM has 512); extra CTAs of a persistent grid only start later.
-    const int by_smem = smem_sm / (ConvCfg<NT>::kSmem + int(fa.sharedSizeBytes) + reserved);
+    const int by_smem =
+        smem_sm / (ConvCfg<NT, MT>::kSmem + int(sizeof(float)) * NT + int(fa.sharedSizeBytes) + reserved);
     const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
     const int by_regs = regs_sm / (warp_regs * (kConvThreads / 32));
-    const int by_tmem = 512 / ConvCfg<NT>::kTmemCols;
+    const int by_tmem = 512 / ConvCfg<NT, MT>::kTmemCols;
     int c = by_smem < by_regs ? by_smem : by_regs;
     c = c < by_tmem ? c : by_tmem;
     ctas_per_sm = c > 0 ? c : 1;
@@ -774,7 +830,8 @@ cudaError_t launch_conv_nt(const ConvArgs& a, const CUtensorMap& tmap, int mtile
   const int ntotal = mtiles * ntiles;
   const int cap = sms * ctas_per_sm;
   const int grid = ntotal < cap ? ntotal : cap;
-  k_conv<NT><<<grid, kConvThreads, ConvCfg<NT>::kSmem, s>>>(a, tmap, ntiles, ntotal);
+  k_conv<NT, MT><<<grid, kConvThreads, ConvCfg<NT, MT>::kSmem + int(sizeof(float)) * a.cout, s>>>(
+      a, tmap, ntiles, ntotal);
   return cudaGetLastError();
 }
 
@@ -808,12 +865,23 @@ cudaError_t run_layer(const Layer& L, int n, unsigned int* err, const float* hea
   a.tw = L.tw;
   a.mask = L.mask.base;
   a.ms = L.mask.stride;
-  const int mtiles = (a.M + kBM - 1) / kBM, ntiles = L.N / L.NT;
+  const int ntiles = L.N / L.NT;
+  if (L.mt == 2) {
+    // units of two tiles: 16 x 16 pixels of one image, or four 8 x 8 images
+    const int units = L.tw == 8 ? (n + 3) / 4 : n * (L.in.H / (2 * kTileH)) * (L.in.W / kTileW);
+    switch (L.NT) {
+      case 16: return launch_conv_nt<16, 2>(a, L.tmap, units, ntiles, s);
+      case 32: return launch_conv_nt<32, 2>(a, L.tmap, units, ntiles, s);
+      case 64: return launch_conv_nt<64, 2>(a, L.tmap, units, ntiles, s);
+      default: return launch_conv_nt<128, 2>(a, L.tmap, units, ntiles, s);
+    }
+  }
+  const int mtiles = (a.M + kBM - 1) / kBM;
   switch (L.NT) {
-    case 16: return launch_conv_nt<16>(a, L.tmap, mtiles, ntiles, s);
-    case 32: return launch_conv_nt<32>(a, L.tmap, mtiles, ntiles, s);
-    case 64: return launch_conv_nt<64>(a, L.tmap, mtiles, ntiles, s);
-    default: return launch_conv_nt<128>(a, L.tmap, mtiles, ntiles, s);
+    case 16: return launch_conv_nt<16, 1>(a, L.tmap, mtiles, ntiles, s);
+    case 32: return launch_conv_nt<32, 1>(a, L.tmap, mtiles, ntiles, s);
+    case 64: return launch_conv_nt<64, 1>(a, L.tmap, mtiles, ntiles, s);
+    default: return launch_conv_nt<128, 1>(a, L.tmap, mtiles, ntiles, s);
   }
 }
 
@@ -1067,8 +1135,13 @@ extern "C" sil_status sil_unet_create(sil_unet** out, const sil_unet_config* cfg
     // the fifth level's 8 x 8 maps are tiled two images at a time
     L.tw = L.in.W >= kTileW ? kTileW : 8;
     if (L.tw == 8 && (L.in.W != 8 || L.in.H != 8 || L.pool || L.head)) st = SIL_EINVAL;
-    // inputs whose channel count is a multiple of 64 are read by tensor map
-    if (L.tma && !encode_input_map(L, B)) L.tma = 0;
+    // inputs whose channel count is a multiple of 64 (or 32) are read by
+    // tensor map, two tiles per stage
+    L.mt = L.tma && L.NT <= 32 ? kUnitTiles : 1;
+    if (L.tma && !encode_input_map(L, B)) {
+      L.tma = 0;
+      L.mt = 1;
+    }
     // weights -> swizzled bf16 blocks [N / NT][KT][NT x 64]
     const size_t blk = size_t(L.NT) * kBK * 2;
     std::vector<uint8_t> h(size_t(L.N / L.NT) * L.KT * blk, 0);
@@ -1859,9 +1932,13 @@ extern "C" sil_status sil_unet_trainer_create(sil_unet_trainer** out, const sil_
     if (mask) G.mask = *mask;
     G.tma = (G.cin_pad % kBK == 0) ? 1 : (G.cin_pad == kBK / 2 && taps == 9) ? 2 : 0;
     G.tw = in.W >= kTileW ? kTileW : 8;
+    G.mt = G.tma && G.NT <= 32 ? kUnitTiles : 1;
     G.bias = tr->zero_bias;
     G.wblk = static_cast<uint8_t*>(dalloc(size_t(G.N) * G.KT * kBK * 2));
-    if (st == SIL_OK && G.tma && !encode_input_map(G, B)) G.tma = 0;
+    if (st == SIL_OK && G.tma && !encode_input_map(G, B)) {
+      G.tma = 0;
+      G.mt = 1;
+    }
     tr->bwd[i] = G;
   };
   for (int l = 0; l < D && st == SIL_OK; ++l) {
