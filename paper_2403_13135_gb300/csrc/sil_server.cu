@@ -59,6 +59,9 @@ struct RingCtl {
   unsigned long long pub;   // requests published (written by the ingest stream)
   unsigned long long cur;   // oldest request that may still have unclaimed chips
   unsigned int err;         // log entries found missing (0 in normal operation)
+  unsigned int idle;        // CTAs that found no chip for idle_ns (reset per launch)
+  unsigned int quit;        // set once every CTA was idle at the same time: all leave
+  unsigned int pad;
 };
 // One publication: request sequence number + 1 (0 = never written), its chip
 // count and slot.
@@ -119,11 +122,22 @@ __global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
       const unsigned long long t0 = gtimer();
       // idle polls back off from 1 to 32 us: a few hundred CTAs polling the
       // ring's two control words every microsecond load one L2 line hard
-      // enough to slow the chips being labelled and the copies
+      // enough to slow the chips being labelled and the copies.  The grid
+      // leaves only as a whole: a CTA idle for idle_ns counts itself idle
+      // and keeps polling; when every CTA is idle at once, the first to see
+      // it sets the quit word and all leave.  (CTAs leaving one by one left
+      // a kernel of a few CTAs that stayed live under a steady trickle of
+      // requests, so the host never relaunched the full grid.)
       unsigned int backoff = 1000;
+      bool counted = false;
       while (true) {
+        if (ld_acquire32(&ctl->quit)) break;
         const unsigned long long pub = ld_acquire(&ctl->pub);
         const unsigned long long cur = ld_acquire(&ctl->cur);
+        if (cur < pub && counted) {
+          atomicSub(&ctl->idle, 1u);
+          counted = false;
+        }
         if (cur < pub) {
           const LogEntry* le = &log[cur % (unsigned long long)L];
           if (ld_acquire(&le->seq1) != cur + 1) {
@@ -158,7 +172,14 @@ __global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
           // request (this cursor value is stale): move the cursor on
           if (exhausted || (w >> 32) != ((cur + 1ull) & 0xffffffffull)) atomicCAS(&ctl->cur, cur, cur + 1ull);
         } else {
-          if ((long long)(gtimer() - t0) > idle_ns) break;
+          if (!counted && (long long)(gtimer() - t0) > idle_ns) {
+            atomicAdd(&ctl->idle, 1u);
+            counted = true;
+          }
+          if (counted && ld_acquire32(&ctl->idle) >= gridDim.x) {
+            atomicExch(&ctl->quit, 1u);
+            break;
+          }
           __nanosleep(backoff);
           backoff = backoff < 32000u ? 2u * backoff : 32000u;
         }
@@ -319,6 +340,7 @@ struct sil_server {
   SlotHost* h_slot = nullptr;          // pinned staging per slot
   LogEntry* h_log = nullptr;           // pinned staging per log entry
   unsigned long long* h_tail = nullptr;  // pinned staging of the published request count, per log entry
+  unsigned int* h_zero = nullptr;        // pinned zeros (the ring's idle and quit words at each launch)
   int L = 0;
   uint64_t next_seq = 0;    // next publication
   uint64_t published = 0;   // chips published
@@ -413,8 +435,14 @@ struct PrepareServed {
 }  // namespace
 
 cudaError_t sil_server::launch() {
-  cudaError_t e = dispatch_served<LaunchServed>(int(dt), dp.need_hs != 0, params.chip <= kResidentChip,
-                                                static_cast<const sil_server*>(this), s_comp);
+  // a new grid starts with no idle CTA and no quit word (the previous grid
+  // has ended: its event completed); a copy from pinned zeros, in stream
+  // order before the kernel
+  cudaError_t e = cudaMemcpyAsync(&d_ctl->idle, h_zero, 3 * sizeof(unsigned int), cudaMemcpyHostToDevice,
+                                  s_comp);
+  if (e == cudaSuccess)
+    e = dispatch_served<LaunchServed>(int(dt), dp.need_hs != 0, params.chip <= kResidentChip,
+                                      static_cast<const sil_server*>(this), s_comp);
   if (e == cudaSuccess) e = cudaEventRecord(ev_kernel, s_comp);
   if (e == cudaSuccess) {
     kernel_live = true;
@@ -670,6 +698,8 @@ sil_status sil_server_create(sil_server** out, const sil_server_config* cfg_in, 
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_slot, sizeof(SlotHost) * R);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_log, sizeof(LogEntry) * s->L);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_tail, sizeof(unsigned long long) * s->L);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_zero, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) memset(s->h_zero, 0, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_kernel, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking);
@@ -876,6 +906,7 @@ void sil_server_destroy(sil_server* srv) {
   cudaFreeHost(srv->h_slot);
   cudaFreeHost(srv->h_log);
   cudaFreeHost(srv->h_tail);
+  cudaFreeHost(srv->h_zero);
   if (srv->ev_kernel) cudaEventDestroy(srv->ev_kernel);
   cudaFree(srv->arena_mem);
   if (srv->s_in) cudaStreamDestroy(srv->s_in);
