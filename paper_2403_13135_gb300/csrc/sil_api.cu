@@ -10,7 +10,7 @@
 #include "sil.h"
 #include "sil_chip.cuh"
 #include "sil_common.h"
-#include "sil_generic.cuh"
+#include "sil_label_kernel.cuh"
 
 namespace sil {
 
@@ -92,74 +92,8 @@ static sil_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 // ---------------------------------------------------------------------------
-// Kernels.
+// Single-request labelling (kernels: sil_label_kernel.cuh).
 // ---------------------------------------------------------------------------
-// Work item k -> chip (cy, cx).  When the grid's last column is narrower
-// than the chip, those chips (the slowest: their last half-warp lanes take a
-// separate path) come first and the rest follow row by row, so that the
-// last wave of the launch holds the bottom row's chips, the cheapest (often
-// shorter than the chip).
-__device__ __forceinline__ void chip_of(int64_t k, const Req& r, int chip, int64_t& cy,
-                                        int64_t& cx) {
-  const bool narrow_last = r.gx > 1 && (r.W % chip) != 0;
-  if (!narrow_last) {
-    cy = k / r.gx;
-    cx = k - cy * r.gx;
-  } else if (k < r.gy) {
-    cy = k;
-    cx = r.gx - 1;
-  } else {
-    const int64_t j = k - r.gy, g = r.gx - 1;
-    cy = j / g;
-    cx = j - cy * g;
-  }
-}
-
-// Chips [0, kend) of the request's grid (in chip_of order), one CTA per chip
-// at a time.
-template <int DT, bool HS>
-__global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
-    k_label(Req r, DevParams dp, int chip, int64_t kend) {
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  __shared__ uint8_t lut[256];
-  __shared__ uint8_t vlut[256];
-  ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
-  for (int64_t k = blockIdx.x; k < kend; k += gridDim.x) {
-    int64_t cy, cx;
-    chip_of(k, r, chip, cy, cx);
-    label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, vlut);
-  }
-}
-
-// Chip kbeg + blockIdx.x / kSplitChip, labelled by a cluster of kSplitChip
-// CTAs (one row slice each).  Used when a request has so few chips that
-// kSplitChip CTAs per chip still fit in one wave: a chip then takes about
-// 0.6 of the time one CTA needs (the statistics and table phases do not
-// shrink with the slice).
-constexpr int kSplitChip = 4;
-__global__ void __cluster_dims__(kSplitChip, 1, 1) __launch_bounds__(kThreadsNarrow, 2)
-    k_label_split(Req r, DevParams dp, int chip, int64_t kbeg) {
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  __shared__ uint8_t lut[256];
-  __shared__ uint8_t vlut[256];
-  ChipSmem<SIL_U8, false>& sm = *reinterpret_cast<ChipSmem<SIL_U8, false>*>(smem_raw);
-  const int64_t k = kbeg + blockIdx.x / kSplitChip;
-  const int64_t cy = k / r.gx, cx = k - cy * r.gx;
-  label_chip<SIL_U8, false, kSplitChip>(r, dp, chip, cy, cx, sm, lut, vlut);
-}
-
-template <int DT, bool HS>
-__global__ void __launch_bounds__(kThreadsNarrow, 2)
-    k_label_generic(Req r, DevParams dp, int chip) {
-  __shared__ __align__(16) ChipStat st;
-  __shared__ uint8_t lut[256];
-  const int64_t nchips = int64_t(r.gx) * r.gy;
-  for (int64_t k = blockIdx.x; k < nchips; k += gridDim.x) {
-    const int64_t cy = k / r.gx, cx = k - cy * r.gx;
-    label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st, lut);
-  }
-}
-
 size_t resident_smem_bytes(int dt, bool hs) {
   if (dt == SIL_U8) return hs ? sizeof(ChipSmem<SIL_U8, true>) : sizeof(ChipSmem<SIL_U8, false>);
   return hs ? sizeof(ChipSmem<SIL_U16, true>) : sizeof(ChipSmem<SIL_U16, false>);
@@ -167,72 +101,14 @@ size_t resident_smem_bytes(int dt, bool hs) {
 
 int device_sm_count();
 
-// Resident CTAs of k_label<SIL_U8, false> on the device (SMs x CTAs per SM).
-static int64_t u8_slots(size_t smem) {
-  static std::once_flag once;
-  static int64_t slots = 0;
-  std::call_once(once, [&] {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_label<SIL_U8, false>, kThreadsNarrow,
-                                                      smem) != cudaSuccess)
-      per_sm = 0;
-    slots = int64_t(per_sm) * device_sm_count();
-    cudaGetLastError();
-  });
-  return slots;
-}
-
-// Whether a grid of n chips goes to the split kernel: when kSplitChip CTAs
-// per chip fit in one wave of resident CTAs.  (Splitting the chips of a
-// last, partly filled wave of a larger grid was measured too: it does not
-// shorten the launch, because the split chips can only start once the full
-// waves end and still take 0.6 of a chip's time.)
-static bool split_all_chips(int64_t n, int64_t slots) {
-  return slots > 0 && n > 0 && n * kSplitChip <= slots;
-}
-
-template <int DT, bool HS>
-static cudaError_t launch_one(const Req& r, const DevParams& dp, int chip,
-                              int grid, cudaStream_t s) {
-  if (chip <= kResidentChip) {
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    const size_t smem = resident_smem_bytes(DT, HS);
-    std::call_once(once, [&] {
-      attr_err = cudaFuncSetAttribute(k_label<DT, HS>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(smem));
-      if (attr_err == cudaSuccess && DT == SIL_U8 && !HS)
-        attr_err = cudaFuncSetAttribute(k_label_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        int(smem));
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    // One CTA of 256 threads per chip: the hardware block scheduler hands
-    // the next chip to whichever slot frees first, which balances chips of
-    // uneven cost (narrow edge chips, chips of one label) better than a
-    // fixed persistent stride (measured 143 vs 162 us on the 10980^2 scene);
-    // 320-thread CTAs were slower at every request size measured (a
-    // 512^2 tile to the 10980^2 scene).
-    const int64_t nchips = int64_t(r.gx) * r.gy;
-    if (DT == SIL_U8 && !HS && split_all_chips(nchips, u8_slots(smem)))
-      k_label_split<<<int(nchips * kSplitChip), kThreadsNarrow, smem, s>>>(r, dp, chip, 0);
-    else
-      k_label<DT, HS><<<grid, kThreadsNarrow, smem, s>>>(r, dp, chip, nchips);
-    return cudaGetLastError();
-  } else {
-    k_label_generic<DT, HS><<<grid, kThreadsNarrow, 0, s>>>(r, dp, chip);
-  }
-  return cudaGetLastError();
-}
-
 cudaError_t launch_label(const Req& r, int dt, const DevParams& dp, int chip,
                          int grid, cudaStream_t s) {
   const bool hs = dp.need_hs != 0;
   if (dt == SIL_U8)
-    return hs ? launch_one<SIL_U8, true>(r, dp, chip, grid, s)
-              : launch_one<SIL_U8, false>(r, dp, chip, grid, s);
-  return hs ? launch_one<SIL_U16, true>(r, dp, chip, grid, s)
-            : launch_one<SIL_U16, false>(r, dp, chip, grid, s);
+    return hs ? LabelKernels<SIL_U8, true>::launch(r, dp, chip, grid, s)
+              : LabelKernels<SIL_U8, false>::launch(r, dp, chip, grid, s);
+  return hs ? LabelKernels<SIL_U16, true>::launch(r, dp, chip, grid, s)
+            : LabelKernels<SIL_U16, false>::launch(r, dp, chip, grid, s);
 }
 
 // Shape / pointer checks shared by the request entry points.

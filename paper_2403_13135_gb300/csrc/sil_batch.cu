@@ -22,13 +22,11 @@
 
 #include "sil.h"
 #include "sil_batch.h"
-#include "sil_chip.cuh"
+#include "sil_batch_kernel.cuh"
 #include "sil_common.h"
-#include "sil_generic.cuh"
 
 namespace sil {
 
-size_t resident_smem_bytes(int dt, bool hs);
 int device_sm_count();
 sil_status check_request(const void* img, int64_t H, int64_t W, int64_t pitch,
                          sil_dtype dt, const uint8_t* labels, int64_t lpitch,
@@ -44,112 +42,29 @@ __global__ void k_batch_prologue(const Req* reqs, int n, unsigned long long* hea
   }
 }
 
-// Tile holding global chip k: largest t with prefix[t] <= k.
-__device__ __forceinline__ int find_tile(const int64_t* prefix, int n, int64_t k) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= k)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
-// Schedules of the batch kernel (chosen by the autotuner):
-//   kSchedStride  persistent CTAs, CTA c labels global chips c, c + grid, ...
-//   kSchedQueue   persistent CTAs taking the next chip from the queue head
-//   kSchedPerChip one CTA per chip (grid = total chips): the hardware block
-//                 scheduler hands chips to slots as they free up
-template <int DT, bool HS, bool RESIDENT, int NT>
-__global__ void __launch_bounds__(NT, (DT == SIL_U8) ? 2 : 1)
-    k_label_batch(const Req* __restrict__ reqs, const int64_t* __restrict__ prefix,
-                  int n, DevParams dp, int chip, unsigned long long* head,
-                  int schedule) {
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  __shared__ uint8_t lut[256];
-  __shared__ long long s_next;
-  __shared__ __align__(16) ChipStat st_generic;
-  const int64_t total = prefix[n];
-  int64_t k = blockIdx.x;
-  if (schedule == kSchedQueue) {
-    if (threadIdx.x == 0) s_next = (long long)atomicAdd(head, 1ull);
-    __syncthreads();
-    k = s_next;
-  }
-  while (k < total) {
-    const int t = find_tile(prefix, n, k);
-    const Req& r = reqs[t];
-    const int64_t local = k - prefix[t];
-    const int64_t cy = local / r.gx, cx = local - cy * r.gx;
-    if (RESIDENT) {
-      ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
-      label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, lut);  // (batches have no V' output)
-    } else {
-      label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st_generic, lut);
-    }
-    if (schedule == kSchedQueue) {
-      __syncthreads();  // everyone has read s_next
-      if (threadIdx.x == 0) s_next = (long long)atomicAdd(head, 1ull);
-      __syncthreads();
-      k = s_next;
-    } else if (schedule == kSchedStride) {
-      k += gridDim.x;
-    } else {
-      break;
-    }
-  }
-}
-
-template <int DT, bool HS, bool RESIDENT>
-static cudaError_t launch_batch_t(const BatchLaunch& b, cudaStream_t s) {
-  const size_t smem = RESIDENT ? resident_smem_bytes(DT, HS) : 0;
-  k_batch_prologue<<<(b.n + 255) / 256, 256, 0, s>>>(b.reqs, b.n, b.head);
-  if (b.threads == kThreadsWide)
-    k_label_batch<DT, HS, RESIDENT, kThreadsWide><<<b.grid, kThreadsWide, smem, s>>>(
-        b.reqs, b.prefix, b.n, b.dp, b.chip, b.head, b.schedule);
-  else
-    k_label_batch<DT, HS, RESIDENT, kThreadsNarrow><<<b.grid, kThreadsNarrow, smem, s>>>(
-        b.reqs, b.prefix, b.n, b.dp, b.chip, b.head, b.schedule);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t s) {
+  k_batch_prologue<<<(b.n + 255) / 256, 256, 0, s>>>(b.reqs, b.n, b.head);
   const bool hs = b.dp.need_hs != 0;
-  const bool res = b.chip <= kResidentChip;
-#define SIL_DISPATCH(DT)                                                  \
-  if (hs)                                                                 \
-    return res ? launch_batch_t<DT, true, true>(b, s)                     \
-               : launch_batch_t<DT, true, false>(b, s);                   \
-  return res ? launch_batch_t<DT, false, true>(b, s)                      \
-             : launch_batch_t<DT, false, false>(b, s);
-  if (b.dt == SIL_U8) {
-    SIL_DISPATCH(SIL_U8)
-  }
-  SIL_DISPATCH(SIL_U16)
-#undef SIL_DISPATCH
+  if (b.dt == SIL_U8)
+    return hs ? BatchKernels<SIL_U8, true>::launch(b, s) : BatchKernels<SIL_U8, false>::launch(b, s);
+  return hs ? BatchKernels<SIL_U16, true>::launch(b, s) : BatchKernels<SIL_U16, false>::launch(b, s);
+}
+
+// The batch kernel instance of a (dtype, H/S, resident, threads) class.
+static const void* batch_fn(int dt, bool hs, bool res, int threads) {
+  if (dt == SIL_U8)
+    return hs ? BatchKernels<SIL_U8, true>::fn(res, threads) : BatchKernels<SIL_U8, false>::fn(res, threads);
+  return hs ? BatchKernels<SIL_U16, true>::fn(res, threads) : BatchKernels<SIL_U16, false>::fn(res, threads);
 }
 
 // Resident CTAs per SM the hardware allows for the batch kernel (the same
 // for both CTA sizes: shared memory is laid out for the larger).
-template <int NT>
-static const void* batch_fn(int dt, bool hs, bool res) {
-#define SIL_F(DT, HS, R) reinterpret_cast<const void*>(k_label_batch<DT, HS, R, NT>)
-  if (dt == SIL_U8)
-    return hs ? (res ? SIL_F(SIL_U8, true, true) : SIL_F(SIL_U8, true, false))
-              : (res ? SIL_F(SIL_U8, false, true) : SIL_F(SIL_U8, false, false));
-  return hs ? (res ? SIL_F(SIL_U16, true, true) : SIL_F(SIL_U16, true, false))
-            : (res ? SIL_F(SIL_U16, false, true) : SIL_F(SIL_U16, false, false));
-#undef SIL_F
-}
-
 int batch_max_ctas_per_sm(int dt, bool hs, int chip) {
   int n = 0;
   const bool res = chip <= kResidentChip;
   const size_t smem = res ? resident_smem_bytes(dt, hs) : 0;
-  const void* fw = batch_fn<kThreadsWide>(dt, hs, res);
-  const void* fn = batch_fn<kThreadsNarrow>(dt, hs, res);
+  const void* fw = batch_fn(dt, hs, res, kThreadsWide);
+  const void* fn = batch_fn(dt, hs, res, kThreadsNarrow);
   if (res) {
     cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
