@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 
 #include "sil.h"
@@ -94,9 +95,76 @@ static sil_status cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 // Single-request labelling (kernels: sil_label_kernel.cuh).
 // ---------------------------------------------------------------------------
-size_t resident_smem_bytes(int dt, bool hs) {
-  if (dt == SIL_U8) return hs ? sizeof(ChipSmem<SIL_U8, true>) : sizeof(ChipSmem<SIL_U8, false>);
-  return hs ? sizeof(ChipSmem<SIL_U16, true>) : sizeof(ChipSmem<SIL_U16, false>);
+namespace {
+struct SmLimits {
+  int smem = 0, regs = 0, reserved = 0, blocks = 0, threads = 0;
+};
+// Per-SM limits of the current device (all devices of a process are taken
+// to be alike).
+const SmLimits& sm_limits() {
+  static std::once_flag once;
+  static SmLimits l;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l.smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&l.regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&l.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&l.blocks, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&l.threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaGetLastError();
+  });
+  return l;
+}
+}  // namespace
+
+template <int DT, bool HS>
+static size_t class_smem_bytes(int threads) {
+  using T = ChipSmem<DT, HS>;
+  return chip_smem_bytes<Px<DT>::BPP, HS || DT == SIL_U16, T::kSmemPlane>(threads);
+}
+
+bool tmem_plane(int dt, bool hs) {
+  if (dt == SIL_U8) return hs ? TmemPlane<SIL_U8, true>::value : TmemPlane<SIL_U8, false>::value;
+  return hs ? TmemPlane<SIL_U16, true>::value : TmemPlane<SIL_U16, false>::value;
+}
+
+size_t resident_smem_bytes(int dt, bool hs, int threads) {
+  size_t b;
+  if (dt == SIL_U8)
+    b = hs ? class_smem_bytes<SIL_U8, true>(threads) : class_smem_bytes<SIL_U8, false>(threads);
+  else
+    b = hs ? class_smem_bytes<SIL_U16, true>(threads) : class_smem_bytes<SIL_U16, false>(threads);
+  if (!tmem_plane(dt, hs)) return b;
+  const int max_ctas = 512 / plane_cols(threads);
+  const int smem_sm = sm_limits().smem > 0 ? sm_limits().smem : 233472;
+  const size_t floor_bytes = size_t(smem_sm / (max_ctas + 1) + 1);
+  return b > floor_bytes ? b : floor_bytes;
+}
+
+int resident_ctas_per_sm(const void* fn, int threads, size_t dyn_smem, int tmem_cols) {
+  const SmLimits& l = sm_limits();
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || l.regs <= 0 || l.smem <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  const int warps = (threads + 31) / 32;
+  const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+  int c = warp_regs > 0 ? l.regs / (warp_regs * warps) : l.blocks;
+  c = std::min(c, l.smem / int(dyn_smem + fa.sharedSizeBytes + size_t(l.reserved)));
+  if (l.threads > 0) c = std::min(c, l.threads / threads);
+  if (l.blocks > 0) c = std::min(c, l.blocks);
+  if (tmem_cols > 0) c = std::min(c, 512 / tmem_cols);
+  return c > 0 ? c : 1;
+}
+
+cudaError_t set_resident_attrs(const void* fn, size_t dyn_smem) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn_smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared));
+  return e;
 }
 
 int device_sm_count();

@@ -57,21 +57,24 @@ static const void* batch_fn(int dt, bool hs, bool res, int threads) {
   return hs ? BatchKernels<SIL_U16, true>::fn(res, threads) : BatchKernels<SIL_U16, false>::fn(res, threads);
 }
 
-// Resident CTAs per SM the hardware allows for the batch kernel (the same
-// for both CTA sizes: shared memory is laid out for the larger).
-int batch_max_ctas_per_sm(int dt, bool hs, int chip) {
-  int n = 0;
+// Resident CTAs per SM the hardware allows for the batch kernel with
+// `threads` threads per CTA; also sets both CTA sizes' shared-memory limits.
+int batch_max_ctas_per_sm(int dt, bool hs, int chip, int threads) {
   const bool res = chip <= kResidentChip;
-  const size_t smem = res ? resident_smem_bytes(dt, hs) : 0;
-  const void* fw = batch_fn(dt, hs, res, kThreadsWide);
-  const void* fn = batch_fn(dt, hs, res, kThreadsNarrow);
-  if (res) {
-    cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  int n = 0;
+  for (int nt : {kThreadsNarrow, kThreadsWide}) {
+    const size_t smem = res ? resident_smem_bytes(dt, hs, nt) : 0;
+    const void* f = batch_fn(dt, hs, res, nt);
+    if (res) set_resident_attrs(f, smem);
+    if (nt != threads) continue;
+    if (res) {
+      n = resident_ctas_per_sm(f, nt, smem, tmem_plane(dt, hs) ? plane_cols(nt) : 0);
+    } else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, nt, 0) != cudaSuccess) {
+      n = 1;
+    }
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fw, kThreadsWide, smem) != cudaSuccess || n < 1)
-    n = 1;
-  return n;
+  cudaGetLastError();
+  return n > 0 ? n : 1;
 }
 
 }  // namespace sil
@@ -314,8 +317,10 @@ sil_status run_batch(const sil_tile* tiles, int32_t n, sil_dtype dt, const sil_p
   const int64_t total = prefix[n];
   int schedule = t.schedule;
   if (schedule == kSchedPerChip && total > int64_t(0x7fffffff)) schedule = kSchedQueue;
+  // CTAs per SM of a persistent schedule: at most what fits with this CTA size
+  const int ctas = std::min(t.ctas, batch_max_ctas_per_sm(int(dt), dp.need_hs != 0, chip, t.threads));
   const int grid = schedule == kSchedPerChip ? int(total)
-                                             : int(std::min<int64_t>(total, int64_t(ctx->sms) * t.ctas));
+                                             : int(std::min<int64_t>(total, int64_t(ctx->sms) * ctas));
   std::vector<uint8_t> key = batch_key(tiles, n, dt, p, grid, schedule, t.threads);
   CachedGraph* hit = nullptr;
   for (auto& g : ctx->graphs)
@@ -360,7 +365,7 @@ sil_status prepare_batch(const char* who, const sil_tile* tiles, int32_t n, sil_
   }
   if ((st = build_batch(tiles, n, dt, p, reqs, prefix)) != SIL_OK) return st;
   const int chip = p ? p->chip : 256;
-  *maxc = batch_max_ctas_per_sm(dt, dp->need_hs != 0, chip);
+  *maxc = batch_max_ctas_per_sm(dt, dp->need_hs != 0, chip, kThreadsNarrow);
   *key = tune_key(ctx, int(dt), dp->need_hs != 0, chip, n, prefix[n]);
   return SIL_OK;
 }
@@ -464,9 +469,10 @@ sil_status sil_autotune_ex(const sil_tile* tiles, int32_t n, sil_dtype dt, const
     Tuning t;
     t.threads = threads;
     t.schedule = kSchedPerChip;
-    t.ctas = maxc;
+    const int maxt = batch_max_ctas_per_sm(int(dt), dp.need_hs != 0, p ? p->chip : 256, threads);
+    t.ctas = maxt;
     cand.push_back(t);
-    for (int c = 1; c <= maxc; ++c) {
+    for (int c = 1; c <= maxt; ++c) {
       t.ctas = c;
       t.schedule = kSchedQueue;
       cand.push_back(t);

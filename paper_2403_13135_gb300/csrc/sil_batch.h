@@ -26,6 +26,6 @@ enum { kSchedStride = 0, kSchedQueue = 1, kSchedPerChip = 2 };
 // batch_max_ctas_per_sm() must have been called once for the same (dt, H/S,
 // chip) class first (it sets the kernel's shared-memory limit).
 cudaError_t launch_batch(const BatchLaunch& b, cudaStream_t s);
-int batch_max_ctas_per_sm(int dt, bool hs, int chip);
+int batch_max_ctas_per_sm(int dt, bool hs, int chip, int threads = kThreadsNarrow);
 
 }  // namespace sil

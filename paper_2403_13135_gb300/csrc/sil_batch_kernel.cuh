@@ -13,8 +13,6 @@
 
 namespace sil {
 
-size_t resident_smem_bytes(int dt, bool hs);
-
 // Tile holding global chip k: largest t with prefix[t] <= k.
 __device__ __forceinline__ int find_tile(const int64_t* prefix, int n, int64_t k) {
   int lo = 0, hi = n - 1;
@@ -34,7 +32,7 @@ __device__ __forceinline__ int find_tile(const int64_t* prefix, int n, int64_t k
 //   kSchedPerChip one CTA per chip (grid = total chips): the hardware block
 //                 scheduler hands chips to slots as they free up
 template <int DT, bool HS, bool RESIDENT, int NT>
-__global__ void __launch_bounds__(NT, (DT == SIL_U8) ? 2 : 1)
+__global__ void __launch_bounds__(NT, RESIDENT ? ResidentCtas<DT, HS, NT>::k : ((DT == SIL_U8) ? 2 : 1))
     k_label_batch(const Req* __restrict__ reqs, const int64_t* __restrict__ prefix,
                   int n, DevParams dp, int chip, unsigned long long* head,
                   int schedule) {
@@ -43,6 +41,9 @@ __global__ void __launch_bounds__(NT, (DT == SIL_U8) ? 2 : 1)
   __shared__ long long s_next;
   __shared__ __align__(16) ChipStat st_generic;
   const int64_t total = prefix[n];
+  constexpr uint32_t kCols = PlaneCols<NT>::kCols;
+  ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
+  if (RESIDENT && !ChipSmem<DT, HS>::kSmemPlane) plane_alloc(&sm.st.tmem, kCols);
   int64_t k = blockIdx.x;
   if (schedule == kSchedQueue) {
     if (threadIdx.x == 0) s_next = (long long)atomicAdd(head, 1ull);
@@ -55,7 +56,6 @@ __global__ void __launch_bounds__(NT, (DT == SIL_U8) ? 2 : 1)
     const int64_t local = k - prefix[t];
     const int64_t cy = local / r.gx, cx = local - cy * r.gx;
     if (RESIDENT) {
-      ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
       label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, lut);  // (batches have no V' output)
     } else {
       label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st_generic, lut);
@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(NT, (DT == SIL_U8) ? 2 : 1)
       break;
     }
   }
+  if (RESIDENT && !ChipSmem<DT, HS>::kSmemPlane) plane_free(sm.st.tmem, kCols);
 }
 
 // The kernel instances of one (dtype, H/S) class.
@@ -85,7 +86,7 @@ struct BatchKernels {
 template <int DT, bool HS>
 cudaError_t BatchKernels<DT, HS>::launch(const BatchLaunch& b, cudaStream_t s) {
   const bool res = b.chip <= kResidentChip;
-  const size_t smem = res ? resident_smem_bytes(DT, HS) : 0;
+  const size_t smem = res ? resident_smem_bytes(DT, HS, b.threads) : 0;
   if (res) {
     if (b.threads == kThreadsWide)
       k_label_batch<DT, HS, true, kThreadsWide><<<b.grid, kThreadsWide, smem, s>>>(

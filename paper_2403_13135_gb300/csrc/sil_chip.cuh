@@ -8,12 +8,13 @@
 //           contiguous 16-byte asynchronous copies, so two rows per band are
 //           in flight while one is computed.
 //           decode -> V = max(R,G,B) -> 3x3 median of V clamped to the chip
-//           -> histogram of Vf in shared memory, Vf kept in a shared plane.
+//           -> histogram of Vf in shared memory, Vf kept in tensor memory
+//           (each thread's own pixels in its own TMEM lane).
 //   stats   all threads: lo/hi, exact Otsu threshold (128-bit compares), gate
 //   LUT     one thread per value: gated min-max stretch, truncation, class
 //           ranges, absdiff override -> label(Vf) table
 //   counts  histogram x table (no per-pixel counting)
-//   pass 2  Vf plane -> table -> uint8 label store
+//   pass 2  Vf from tensor memory -> table -> uint8 label store
 //
 // Paper passages: Sec. III-B "Filtering Out the Thin Clouds and Shadows"
 // (HSV, noise filtering, Otsu, min-max normalisation, truncation, absolute
@@ -33,6 +34,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "sil_common.h"
@@ -45,7 +47,6 @@ constexpr int kMaxBands = kMaxThreads / 16;  // one row band per half-warp
 __device__ __forceinline__ int n_warps() { return int(blockDim.x) >> 5; }
 __device__ __forceinline__ int n_bands() { return int(blockDim.x) >> 4; }
 constexpr int kBinWarps = 256 / 32;  // warps whose threads own a histogram bin
-constexpr int kPlaneStride = 256;
 #ifndef SIL_RING
 #define SIL_RING 3
 #endif
@@ -59,6 +60,7 @@ struct ChipStat {
   uint32_t red[kMaxWarps][4];
   uint32_t nod[kMaxWarps];
   int32_t stat[8];
+  uint32_t tmem;  // tensor-memory address of the CTA's Vf plane (resident kernels)
 };
 // Scratch of the block-wide Otsu search.
 struct alignas(16) StatScratch {
@@ -79,16 +81,118 @@ struct Slot {
 
 // Shared memory of the resident kernel.  The statistics come first so the
 // histogram sits at shared offset 0 and a bin's byte offset is its address.
-template <int BPP, bool FLAGS>
+// The row ring comes last: it is declared for the largest CTA, but a launch
+// allocates only the blockDim.x / 16 bands it uses (resident_smem_bytes).
+// The filtered V plane is here only when SPLANE; otherwise it lives in
+// tensor memory (below).
+template <int BPP, bool FLAGS, bool SPLANE>
 struct ChipSmemT {
+  static constexpr bool kSmemPlane = SPLANE;
   ChipStat st;
   StatScratch sc;
-  alignas(16) uint8_t ring[kMaxBands][kRing][Slot<BPP>::kBytes];
-  alignas(16) uint8_t vf[256 * kPlaneStride];  // filtered V, plane order
   // per row, per lane: 16 nibbles (bits 0-2 class mask of the H/S ranges,
   // bit 3 nodata); uint16 and H/S-narrowed variants only
   uint32_t flags[FLAGS ? 256 : 1][FLAGS ? 16 : 1][FLAGS ? 2 : 1];
+  // filtered V in shared memory (plane order, 256 bytes a row)
+  alignas(16) uint8_t vf[SPLANE ? 256 * 256 : 16];
+  alignas(16) uint8_t ring[kMaxBands][kRing][Slot<BPP>::kBytes];
 };
+// Bytes of ChipSmemT used by a CTA of nt threads.
+template <int BPP, bool FLAGS, bool SPLANE>
+constexpr size_t chip_smem_bytes(int nt) {
+  using T = ChipSmemT<BPP, FLAGS, SPLANE>;
+  return offsetof(T, ring) + size_t(nt / 16) * kRing * Slot<BPP>::kBytes;
+}
+
+// ---------------------------------------------------------------------------
+// The filtered V plane in tensor memory.  Pass 2 reads back exactly the
+// pixels each thread filtered in pass 1, so the plane is per-thread data:
+// thread (warp w, lane l) keeps the 4 plane words of each of its band rows
+// in TMEM lane 32 (w % 4) + l (the lane quarter warp w may access), columns
+// 64 (w / 4) + 4 j .. + 3 for band row j (a band has at most 16 rows).  A
+// CTA of up to 8 warps allocates 128 columns (64 KB), of 10 warps 256.
+// Keeping the plane out of shared memory leaves a 256-thread u8 CTA about
+// 40 KB of shared memory, so three of them (register-bound) share an SM;
+// the block scheduler does not count tensor memory, so the host keeps the
+// CTAs an SM can hold times these columns within its 512 (see
+// resident_smem_bytes).
+// ---------------------------------------------------------------------------
+// Whether the resident kernels of a (dtype, H/S) class keep the plane in
+// tensor memory (else in shared memory).
+template <int DT, bool HS>
+struct TmemPlane {
+  static constexpr bool value = true;
+};
+template <int NT>
+struct PlaneCols {
+  static constexpr uint32_t kCols = NT <= 256 ? 128u : 256u;
+};
+// CTAs per SM the resident kernels of 256 threads are compiled for (the
+// register budget): three for 8-bit images without H/S ranges (80
+// registers), two for 16-bit images (the ring takes half of an SM's shared
+// memory) and for 8-bit images with H/S ranges (which spill at 80), one for
+// 16-bit images with H/S ranges (which spill at 128).  CTAs of 320
+// threads: two.
+template <int DT, bool HS, int NT = kThreadsNarrow>
+struct ResidentCtas {
+  static constexpr int k = NT != kThreadsNarrow         ? 2
+                           : !TmemPlane<DT, HS>::value  ? (DT == SIL_U8 ? 2 : 1)
+                           : (DT == SIL_U8 && !HS)      ? 3
+                           : (DT == SIL_U16 && HS)      ? 1
+                                                        : 2;
+};
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// Allocates the CTA's plane (warp 0) and publishes its address in *slot.
+// All threads must call it.
+__device__ __forceinline__ void plane_alloc(uint32_t* slot, uint32_t cols) {
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(slot)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Frees it once every thread's plane accesses have completed.  All threads
+// must call it.
+__device__ __forceinline__ void plane_free(uint32_t base, uint32_t cols) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols)
+                 : "memory");
+}
+// This thread's plane address (band row 0).
+__device__ __forceinline__ uint32_t plane_taddr(uint32_t base) {
+  const uint32_t w = threadIdx.x >> 5;
+  return base + ((32u * (w & 3u)) << 16) + 64u * (w >> 2);
+}
+// Warp-wide (every lane, the same column): one band row's 4 plane words.
+__device__ __forceinline__ void plane_st(uint32_t taddr, uint4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void plane_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// Warp-wide: four band rows' plane words (16 columns), waited for.
+__device__ __forceinline__ void plane_ld4rows(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
 
 enum { kStatLo = 0, kStatHi, kStatT, kStatN0, kStatGate, kStatN };
 
@@ -108,7 +212,9 @@ __device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, ui
                                           const DevParams& dp) {
   return imad(d, dp.sh24, imad(c, dp.sh16, imad(b, dp.sh8, a)));
 }
-// a + b + c - x - y, exact modulo 2^32 (the two subtractions as multiply-adds)
+// a + b + c - x - y, exact modulo 2^32 (the two subtractions as multiply-adds;
+// doing the two additions as multiply-adds too was measured slower: the
+// longer dependency chain costs more than the min/max pipe saves)
 __device__ __forceinline__ uint32_t sum3m2(uint32_t a, uint32_t b, uint32_t c, uint32_t x,
                                            uint32_t y, const DevParams& dp) {
   return imad(y, dp.neg1, imad(x, dp.neg1, a + b + c));
@@ -165,8 +271,18 @@ __device__ __forceinline__ void copy_row_full(uint8_t* slot, const uint8_t* rowp
   constexpr int kBlocks = BPP * 256 / 16;  // a multiple of 16
   const uintptr_t A = (reinterpret_cast<uintptr_t>(rowptr) & ~uintptr_t(15)) + 16u * uintptr_t(q);
   const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(slot)) + 16u * uint32_t(q);
+  if constexpr (kBlocks == 48) {
+    // one predicate for the lane's three copies
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t"
+        "@p cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+        "@p cp.async.cg.shared.global [%0+256], [%1+256], 16;\n\t"
+        "@p cp.async.cg.shared.global [%0+512], [%1+512], 16;\n\t}" ::"r"(dst),
+        "l"(A), "r"(uint32_t(go)) : "memory");
+  } else {
 #pragma unroll
-  for (int t = 0; t < kBlocks / 16; ++t) cp16_if(dst + 256u * uint32_t(t), A + 256u * uintptr_t(t), go);
+    for (int t = 0; t < kBlocks / 16; ++t) cp16_if(dst + 256u * uint32_t(t), A + 256u * uintptr_t(t), go);
+  }
   cp16_if(dst + 16u * kBlocks, A + 16u * kBlocks, go && q == 0 && m != 0);
 }
 __device__ __forceinline__ void commit_rows() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -372,11 +488,15 @@ struct RowBuf {
 
 // Output row y from the window rows (M, Z, P) = (y-1, y, y+1): 3x3 median as
 // med3(max3 of column minima, med3 of column medians, min3 of column maxima),
-// histogram of Vf, Vf plane row.
-template <bool kFlags, int DT, bool FULL, class SM>
+// histogram of Vf, Vf plane row (tensor memory at taddr).  CHECK: the row
+// may lie past this half-warp's band (live false: the other half-warp of
+// the warp has one row more, and the plane store is warp-wide), so the
+// histogram and the flags are skipped then.
+template <bool kFlags, int DT, bool FULL, bool CHECK, class SM>
 __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const RowBuf& P,
                                          int y, int q, int nvalid, bool use_median,
-                                         const DevParams& dp, SM& sm, uint32_t& n_nodata) {
+                                         const DevParams& dp, SM& sm, uint32_t& n_nodata,
+                                         uint32_t taddr, bool live) {
   uint32_t out[8];
   if (use_median) {
     uint32_t L[10], X[10], C[10];
@@ -408,7 +528,9 @@ __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const
   // Histogram of Vf over valid, non-nodata pixels; the bin index is byte 1
   // (low lane) or byte 3 (high lane) of each word.
   uint32_t* hist = sm.st.hist;
-  if (!kFlags && FULL) {
+  if (CHECK && !live) {
+    // a row past the band: filtered only for the warp-wide plane store
+  } else if (!kFlags && FULL) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       // low lane: byte 1 by a permute; high lane: byte 3 = the high word of
@@ -445,10 +567,15 @@ __device__ __forceinline__ void emit_row(const RowBuf& M, const RowBuf& Z, const
   pw.y = __byte_perm(out[2], out[3], 0x7351);
   pw.z = __byte_perm(out[4], out[5], 0x7351);
   pw.w = __byte_perm(out[6], out[7], 0x7351);
-  *reinterpret_cast<uint4*>(&sm.vf[y * kPlaneStride + 16 * q]) = pw;
-  if (kFlags) {
+  if (kFlags && (!CHECK || live)) {
     sm.flags[y][q][0] = Z.f[0];
     sm.flags[y][q][1] = Z.f[1];
+  }
+  if constexpr (SM::kSmemPlane) {
+    if (!CHECK || live) *reinterpret_cast<uint4*>(&sm.vf[y * 256 + 16 * q]) = pw;
+  } else {
+    if (kFlags || CHECK) __syncwarp();  // the lanes took different branches above
+    plane_st(taddr, pw);
   }
 }
 
@@ -484,10 +611,15 @@ __device__ __forceinline__ void band_issue(const Band& b, uint8_t* slot, int k, 
 // slot with row k + 3.  The row loop is unrolled by three so that the window
 // rows (y-1, y, y+1) rotate through three register sets and each slot index
 // is a constant.  FULL: every lane has 16 columns (chip width 256).  A4:
-// every row of the chip starts on a 4-byte boundary.
+// every row of the chip starts on a 4-byte boundary.  The two half-warps of
+// a warp step through the same number of rows, nmax (their bands differ by
+// at most one row, nmin <= r1 - r0 <= nmax), because the plane store is a
+// warp-wide instruction: a half-warp's extra row filters a clamped row of
+// the chip and stores it to a plane column that pass 2 does not read.
 template <int DT, bool HS, bool FULL, bool A4, class SM>
 __device__ __forceinline__ void band_pass1(const Band& b, const DevParams& dp, SM& sm,
-                                           uint32_t& n_nodata) {
+                                           uint32_t& n_nodata, int nmin, int nmax,
+                                           uint32_t taddr) {
   constexpr int BPP = Px<DT>::BPP;
   constexpr bool kFlags = HS || DT == SIL_U16;
   constexpr int SB = Slot<BPP>::kBytes;
@@ -495,10 +627,10 @@ __device__ __forceinline__ void band_pass1(const Band& b, const DevParams& dp, S
   const int lane = threadIdx.x & 31, band = threadIdx.x >> 4;
   const int q = lane & 15;
   const uint32_t hmask = 0xFFFFu << (lane & 16);
-  const int w = b.w, r0 = b.r0, r1 = b.r1;
+  const int w = b.w, r0 = b.r0, own = b.r1 - b.r0;
   const int nvalid = FULL ? 16 : min(max(w - 16 * q, 0), 16);
   const bool use_median = dp.filter && dp.median;
-  const int nrows = r1 - r0 + 2;  // streamed rows 0 .. r1 - r0 + 1
+  const int nrows = nmax + 2;  // streamed rows 0 .. nmax + 1
   uint8_t* const s0 = sm.ring[band][0];
   uint8_t* const s1 = s0 + SB;
   uint8_t* const s2 = s1 + SB;
@@ -519,26 +651,35 @@ __device__ __forceinline__ void band_pass1(const Band& b, const DevParams& dp, S
     commit_rows();
     edge_words(B.v, q, w, hmask, B.eL, B.eR);
   };
+#define SIL_EMIT(CHK, M, Z, P, J) \
+  emit_row<kFlags, DT, FULL, CHK>(M, Z, P, r0 + (J), q, nvalid, use_median, dp, sm, n_nodata, \
+                                  taddr + 4u * uint32_t(J), (J) < own)
   RowBuf B0, B1, B2;
   step(B0, s0, m0, 0);
   step(B1, s1, m1, 1);
-  int y = r0, k = 2;
-  for (; y + 3 <= r1; y += 3, k += 3) {
-    step(B2, s2, m2, k);
-    emit_row<kFlags, DT, FULL>(B0, B1, B2, y, q, nvalid, use_median, dp, sm, n_nodata);
-    step(B0, s0, m0, k + 1);
-    emit_row<kFlags, DT, FULL>(B1, B2, B0, y + 1, q, nvalid, use_median, dp, sm, n_nodata);
-    step(B1, s1, m1, k + 2);
-    emit_row<kFlags, DT, FULL>(B2, B0, B1, y + 2, q, nvalid, use_median, dp, sm, n_nodata);
+  int j = 0;
+  for (; j + 3 <= nmin; j += 3) {
+    step(B2, s2, m2, j + 2);
+    SIL_EMIT(false, B0, B1, B2, j);
+    step(B0, s0, m0, j + 3);
+    SIL_EMIT(false, B1, B2, B0, j + 1);
+    step(B1, s1, m1, j + 4);
+    SIL_EMIT(false, B2, B0, B1, j + 2);
   }
-  if (y < r1) {
-    step(B2, s2, m2, k);
-    emit_row<kFlags, DT, FULL>(B0, B1, B2, y, q, nvalid, use_median, dp, sm, n_nodata);
-    if (y + 1 < r1) {
-      step(B0, s0, m0, k + 1);
-      emit_row<kFlags, DT, FULL>(B1, B2, B0, y + 1, q, nvalid, use_median, dp, sm, n_nodata);
+  // at most three rows are left (nmin - j <= 2, nmax - nmin <= 1)
+  if (j < nmax) {
+    step(B2, s2, m2, j + 2);
+    SIL_EMIT(true, B0, B1, B2, j);
+    if (j + 1 < nmax) {
+      step(B0, s0, m0, j + 3);
+      SIL_EMIT(true, B1, B2, B0, j + 1);
+      if (j + 2 < nmax) {
+        step(B1, s1, m1, j + 4);
+        SIL_EMIT(true, B2, B0, B1, j + 2);
+      }
     }
   }
+#undef SIL_EMIT
   // every copy this band issued for the chip has been waited for (the
   // groups committed after the last row's copy are empty)
 }
@@ -878,15 +1019,14 @@ __device__ __forceinline__ void store_row16(uint8_t* dst, int nvalid, uint4 lab)
     if (j < nvalid) dst[j] = uint8_t(wv[j >> 2] >> (8 * (j & 3)));
 }
 
-// Store of a lane's 16 labels.  STORE: every label row of the chip starts
-// on a 16-byte (16) or 4-byte (4) boundary, or neither (1); known per chip,
-// so the choice is not made per row.  Lanes with fewer than 16 columns left
-// (the right edge of a narrow chip) store bytes.
-template <int STORE>
-__device__ __forceinline__ void store_labels(uint8_t* dst, int nvalid, uint4 lab) {
-  if (STORE == 16 && nvalid == 16) {
+// Store of a lane's 16 labels.  store: every label row of the chip starts
+// on a 16-byte (16) or 4-byte (4) boundary, or neither (1); known per chip
+// (a branch every lane of the chip takes alike).  Lanes with fewer than 16
+// columns left (the right edge of a narrow chip) store bytes.
+__device__ __forceinline__ void store_labels(uint8_t* dst, int nvalid, uint4 lab, int store) {
+  if (store == 16 && nvalid == 16) {
     *reinterpret_cast<uint4*>(dst) = lab;
-  } else if (STORE == 4 && nvalid == 16) {
+  } else if (store == 4 && nvalid == 16) {
     uint32_t* d = reinterpret_cast<uint32_t*>(dst);
     d[0] = lab.x;
     d[1] = lab.y;
@@ -900,19 +1040,45 @@ __device__ __forceinline__ void store_labels(uint8_t* dst, int nvalid, uint4 lab
   }
 }
 
-template <int DT, bool HS, int STORE, bool FULL, class SM>
+// Rows are read from the plane four at a time (one warp-wide load of 16
+// columns; the warp steps through nmax rows, see band_pass1); rows past the
+// half-warp's band and lanes past the chip's last column store nothing.
+template <int DT, bool HS, class SM>
 __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int64_t y0, int64_t x0,
-                                           int w, int r0, int r1, const uint8_t* lut, const SM& sm,
-                                           uint32_t* cnt, const DevParams& dp) {
+                                           int w, int r0, int r1, int nmax, uint32_t taddr,
+                                           const uint8_t* lut, const SM& sm, uint32_t* cnt,
+                                           const DevParams& dp, int store) {
   constexpr bool kFlags = HS || DT == SIL_U16;
   const int q = threadIdx.x & 15;
-  const int nvalid = FULL ? 16 : min(max(w - 16 * q, 0), 16);
-  if (nvalid == 0) return;
+  const int nvalid = min(max(w - 16 * q, 0), 16);
+  const int own = nvalid > 0 ? r1 - r0 : 0;
   uint8_t* dst = labels ? labels + (y0 + r0) * lpitch + x0 + 16 * q : nullptr;
-  for (int y = r0; y < r1; ++y) {
-    const uint4 pw = *reinterpret_cast<const uint4*>(&sm.vf[y * kPlaneStride + 16 * q]);
+  for (int j0 = 0; j0 < nmax; j0 += 4) {
+    uint32_t pr[16];
+    if constexpr (SM::kSmemPlane) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (j0 + i < own) {
+          const uint4 pw = *reinterpret_cast<const uint4*>(&sm.vf[(r0 + j0 + i) * 256 + 16 * q]);
+          pr[4 * i] = pw.x;
+          pr[4 * i + 1] = pw.y;
+          pr[4 * i + 2] = pw.z;
+          pr[4 * i + 3] = pw.w;
+        }
+      }
+    } else {
+      __syncwarp();
+      plane_ld4rows(taddr + 4u * uint32_t(j0), pr);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+    if (j0 + i >= own) break;
+    // one row's table lookups at a time (kept from being hoisted above the
+    // previous row's stores, which would hold 64 lookups in registers)
+    asm volatile("" ::: "memory");
+    const int y = r0 + j0 + i;
     // plane word k holds columns (2k, 2k+1, 2k+8, 2k+9)
-    const uint32_t p[4] = {pw.x, pw.y, pw.z, pw.w};
+    const uint32_t p[4] = {pr[4 * i], pr[4 * i + 1], pr[4 * i + 2], pr[4 * i + 3]};
     uint32_t l[16];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -946,8 +1112,9 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
       lab.y = pack4(l[4], l[5], l[6], l[7], dp);
       lab.z = pack4(l[8], l[9], l[10], l[11], dp);
       lab.w = pack4(l[12], l[13], l[14], l[15], dp);
-      store_labels<STORE>(dst, nvalid, lab);
+      store_labels(dst, nvalid, lab, store);
       dst += lpitch;
+    }
     }
   }
 }
@@ -956,15 +1123,34 @@ __device__ __forceinline__ void band_pass2(uint8_t* labels, int64_t lpitch, int6
 // (0 for nodata), rows r0..r1-1 of the band.
 template <bool kFlags, class SM>
 __device__ __forceinline__ void band_vprime(uint8_t* out, int64_t pitch, int64_t y0, int64_t x0,
-                                            int w, int r0, int r1, const uint8_t* vlut,
-                                            const SM& sm) {
+                                            int w, int r0, int r1, int nmax, uint32_t taddr,
+                                            const uint8_t* vlut, const SM& sm) {
   const int q = threadIdx.x & 15;
   const int nvalid = min(max(w - 16 * q, 0), 16);
-  if (nvalid == 0) return;
+  const int own = nvalid > 0 ? r1 - r0 : 0;
   uint8_t* dst = out + (y0 + r0) * pitch + x0 + 16 * q;
-  for (int y = r0; y < r1; ++y, dst += pitch) {
-    const uint4 pw = *reinterpret_cast<const uint4*>(&sm.vf[y * kPlaneStride + 16 * q]);
-    const uint32_t p[4] = {pw.x, pw.y, pw.z, pw.w};
+  for (int j0 = 0; j0 < nmax; j0 += 4) {
+    uint32_t pr[16];
+    if constexpr (SM::kSmemPlane) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (j0 + i < own) {
+          const uint4 pw = *reinterpret_cast<const uint4*>(&sm.vf[(r0 + j0 + i) * 256 + 16 * q]);
+          pr[4 * i] = pw.x;
+          pr[4 * i + 1] = pw.y;
+          pr[4 * i + 2] = pw.z;
+          pr[4 * i + 3] = pw.w;
+        }
+      }
+    } else {
+      __syncwarp();
+      plane_ld4rows(taddr + 4u * uint32_t(j0), pr);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+    if (j0 + i >= own) break;
+    const int y = r0 + j0 + i;
+    const uint32_t p[4] = {pr[4 * i], pr[4 * i + 1], pr[4 * i + 2], pr[4 * i + 3]};
     uint32_t l[16];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -985,6 +1171,8 @@ __device__ __forceinline__ void band_vprime(uint8_t* out, int64_t pitch, int64_t
     v.z = __byte_perm(__byte_perm(l[8], l[9], 0x0040), __byte_perm(l[10], l[11], 0x0040), 0x5410);
     v.w = __byte_perm(__byte_perm(l[12], l[13], 0x0040), __byte_perm(l[14], l[15], 0x0040), 0x5410);
     store_row16(dst, nvalid, v);
+    dst += pitch;
+    }
   }
 }
 
@@ -1030,27 +1218,35 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
   if (kSplit > 1) rank = cooperative_groups::this_cluster().block_rank();
   const Band bd = chip_band<DT>(r, chip, cy, cx, kSplit, rank);
   const int r0 = bd.r0, r1 = bd.r1;
+  // rows of this half-warp's band and of the other half-warp's (the warp
+  // steps through nmax rows in both passes)
+  const int own = r1 - r0, other = __shfl_xor_sync(0xffffffffu, own, 16);
+  const int nmin = min(own, other), nmax = max(own, other);
+  const uint32_t taddr = plane_taddr(sm.st.tmem);
 
   __syncthreads();  // the previous chip of a persistent CTA is done with sm
   if (tid < 256) sm.st.hist[tid] = 0;
   __syncthreads();
   uint32_t n_nodata = 0;
-  if (r0 < r1) {
+  if (nmax > 0) {
     // rows start on 4-byte boundaries when the base, the pitch and the chip's
     // first column (x0 * 3 or x0 * 6 bytes) do
     const bool a4 = ((reinterpret_cast<uintptr_t>(r.img) | uint64_t(r.pitch) | uint64_t(x0)) & 3) == 0;
+#define SIL_PASS1(F, A) band_pass1<DT, HS, F, A>(bd, dp, sm, n_nodata, nmin, nmax, taddr)
     if (w == 256) {
       if (a4)
-        band_pass1<DT, HS, true, true>(bd, dp, sm, n_nodata);
+        SIL_PASS1(true, true);
       else
-        band_pass1<DT, HS, true, false>(bd, dp, sm, n_nodata);
+        SIL_PASS1(true, false);
     } else {
       if (a4)
-        band_pass1<DT, HS, false, true>(bd, dp, sm, n_nodata);
+        SIL_PASS1(false, true);
       else
-        band_pass1<DT, HS, false, false>(bd, dp, sm, n_nodata);
+        SIL_PASS1(false, false);
     }
+#undef SIL_PASS1
   }
+  if constexpr (!SM::kSmemPlane) plane_wait_st();  // this thread's plane rows are in tensor memory
   if (DT == SIL_U16) {
     n_nodata = __reduce_add_sync(0xffffffffu, n_nodata);
     if (lane == 0) sm.st.nod[wid] = n_nodata;
@@ -1113,23 +1309,13 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
         for (int y = r0; y < r1; ++y, dst += r.lpitch) store_row16(dst, nvalid, make_uint4(cw, cw, cw, cw));
       }
     }
-  } else if (r0 < r1 && (HS || r.labels)) {
+  } else if (nmax > 0 && (HS || r.labels)) {
     const uint64_t la = reinterpret_cast<uintptr_t>(r.labels) + uint64_t(x0);
     const int store = ((la | uint64_t(r.lpitch)) & 15) == 0 ? 16 : ((la | uint64_t(r.lpitch)) & 3) == 0 ? 4 : 1;
-#define SIL_PASS2(S, F) band_pass2<DT, HS, S, F>(r.labels, r.lpitch, y0, x0, w, r0, r1, lut, sm, cnt, dp)
-    if (w == 256) {
-      if (store == 16) SIL_PASS2(16, true);
-      else if (store == 4) SIL_PASS2(4, true);
-      else SIL_PASS2(1, true);
-    } else {
-      if (store == 16) SIL_PASS2(16, false);
-      else if (store == 4) SIL_PASS2(4, false);
-      else SIL_PASS2(1, false);
-    }
-#undef SIL_PASS2
+    band_pass2<DT, HS>(r.labels, r.lpitch, y0, x0, w, r0, r1, nmax, taddr, lut, sm, cnt, dp, store);
   }
-  if (r.vprime && r0 < r1)
-    band_vprime<HS || DT == SIL_U16>(r.vprime, r.vpitch, y0, x0, w, r0, r1, vlut, sm);
+  if (r.vprime && nmax > 0)
+    band_vprime<HS || DT == SIL_U16>(r.vprime, r.vpitch, y0, x0, w, r0, r1, nmax, taddr, vlut, sm);
   if (HS) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -1153,6 +1339,6 @@ __device__ __forceinline__ void label_chip(const Req& r, const DevParams& dp, in
 }
 
 template <int DT, bool HS>
-using ChipSmem = ChipSmemT<Px<DT>::BPP, HS || DT == SIL_U16>;
+using ChipSmem = ChipSmemT<Px<DT>::BPP, HS || DT == SIL_U16, !TmemPlane<DT, HS>::value>;
 
 }  // namespace sil

@@ -1,6 +1,9 @@
 // sil_common.h -- host/device shared definitions of libsil (not part of the
 // public ABI; the public header is include/sil.h).
 #pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
 #include <cstdint>
 
 #include "sil.h"
@@ -50,6 +53,27 @@ constexpr int kResidentChip = 256;
 constexpr int kThreadsNarrow = 256;
 constexpr int kThreadsWide = 320;
 constexpr int kMaxThreads = kThreadsWide;
+
+// Dynamic shared memory of a resident chip kernel of `threads` threads
+// (the layout up to the row ring plus threads / 16 ring bands), raised where
+// needed so that no more CTAs fit an SM than its tensor memory holds planes
+// for: the block scheduler does not count tensor memory, and an allocation
+// beyond an SM's 512 columns would wait for another CTA to finish.
+size_t resident_smem_bytes(int dt, bool hs, int threads = kThreadsNarrow);
+// Tensor-memory columns of a resident chip kernel's plane.
+inline int plane_cols(int threads) { return threads <= 256 ? 128 : 256; }
+// Whether the resident kernels of a (dtype, H/S) class keep their plane in
+// tensor memory.
+bool tmem_plane(int dt, bool hs);
+// CTAs of kernel fn (threads per CTA, dynamic shared memory dyn_smem) that
+// one SM holds at once, from its registers, shared memory and threads, and
+// at most 512 / tmem_cols when it allocates tensor memory (the occupancy
+// calculator reports one CTA per SM for any kernel that does).
+int resident_ctas_per_sm(const void* fn, int threads, size_t dyn_smem, int tmem_cols);
+// Sets a resident chip kernel's dynamic shared-memory limit and asks for the
+// largest shared-memory carveout (its CTAs share an SM by shared memory;
+// its global accesses bypass L1).
+cudaError_t set_resident_attrs(const void* fn, size_t dyn_smem);
 
 // Validates p and derives DevParams; returns SIL_OK or SIL_EINVAL with a
 // message stored for sil_last_error().

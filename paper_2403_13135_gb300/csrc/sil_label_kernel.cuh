@@ -13,7 +13,6 @@
 
 namespace sil {
 
-size_t resident_smem_bytes(int dt, bool hs);
 int device_sm_count();
 
 // Work item k -> chip (cy, cx).  When the grid's last column is narrower
@@ -37,20 +36,22 @@ __device__ __forceinline__ void chip_of(int64_t k, const Req& r, int chip, int64
   }
 }
 
-// Chips [0, kend) of the request's grid (in chip_of order), one CTA per chip
-// at a time.
+// Chip blockIdx.x of the request's grid (in chip_of order): one CTA per
+// chip, so the hardware block scheduler hands the next chip to whichever
+// slot frees first (and no chip loop keeps registers live across a chip).
 template <int DT, bool HS>
-__global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
-    k_label(Req r, DevParams dp, int chip, int64_t kend) {
+__global__ void __launch_bounds__(kThreadsNarrow, (ResidentCtas<DT, HS>::k))
+    k_label(Req r, DevParams dp, int chip) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   __shared__ uint8_t lut[256];
   __shared__ uint8_t vlut[256];
   ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
-  for (int64_t k = blockIdx.x; k < kend; k += gridDim.x) {
-    int64_t cy, cx;
-    chip_of(k, r, chip, cy, cx);
-    label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, vlut);
-  }
+  constexpr uint32_t kCols = PlaneCols<kThreadsNarrow>::kCols;
+  if (!ChipSmem<DT, HS>::kSmemPlane) plane_alloc(&sm.st.tmem, kCols);
+  int64_t cy, cx;
+  chip_of(blockIdx.x, r, chip, cy, cx);
+  label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, vlut);
+  if (!ChipSmem<DT, HS>::kSmemPlane) plane_free(sm.st.tmem, kCols);
 }
 
 // Chip kbeg + blockIdx.x / kSplitChip, labelled by a cluster of kSplitChip
@@ -60,16 +61,20 @@ __global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
 // shrink with the slice).
 constexpr int kSplitChip = 4;
 template <int DT>
-__global__ void __cluster_dims__(kSplitChip, 1, 1) __launch_bounds__(kThreadsNarrow, 2)
+__global__ void __cluster_dims__(kSplitChip, 1, 1)
+    __launch_bounds__(kThreadsNarrow, (ResidentCtas<SIL_U8, false>::k))
     k_label_split(Req r, DevParams dp, int chip, int64_t kbeg) {
   static_assert(DT == SIL_U8, "the split kernel serves u8 requests");
   extern __shared__ __align__(128) uint8_t smem_raw[];
   __shared__ uint8_t lut[256];
   __shared__ uint8_t vlut[256];
   ChipSmem<SIL_U8, false>& sm = *reinterpret_cast<ChipSmem<SIL_U8, false>*>(smem_raw);
+  constexpr uint32_t kCols = PlaneCols<kThreadsNarrow>::kCols;
+  if (!ChipSmem<SIL_U8, false>::kSmemPlane) plane_alloc(&sm.st.tmem, kCols);
   const int64_t k = kbeg + blockIdx.x / kSplitChip;
   const int64_t cy = k / r.gx, cx = k - cy * r.gx;
   label_chip<SIL_U8, false, kSplitChip>(r, dp, chip, cy, cx, sm, lut, vlut);
+  if (!ChipSmem<SIL_U8, false>::kSmemPlane) plane_free(sm.st.tmem, kCols);
 }
 
 template <int DT, bool HS>
@@ -108,12 +113,9 @@ int64_t LabelKernels<DT, HS>::slots(size_t smem) {
   static std::once_flag once;
   static int64_t n = 0;
   std::call_once(once, [&] {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_label<DT, HS>, kThreadsNarrow,
-                                                      smem) != cudaSuccess)
-      per_sm = 0;
+    const int per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(k_label<DT, HS>),
+                                            kThreadsNarrow, smem, tmem_plane(DT, HS) ? plane_cols(kThreadsNarrow) : 0);
     n = int64_t(per_sm) * device_sm_count();
-    cudaGetLastError();
   });
   return n;
 }
@@ -124,32 +126,31 @@ cudaError_t LabelKernels<DT, HS>::launch(const Req& r, const DevParams& dp, int 
   if (chip <= kResidentChip) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
-    const size_t smem = resident_smem_bytes(DT, HS);
+    const size_t smem = resident_smem_bytes(DT, HS, kThreadsNarrow);
     std::call_once(once, [&] {
-      attr_err = cudaFuncSetAttribute(k_label<DT, HS>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(smem));
+      attr_err = set_resident_attrs(reinterpret_cast<const void*>(k_label<DT, HS>), smem);
       if constexpr (DT == SIL_U8 && !HS) {
         if (attr_err == cudaSuccess)
-          attr_err = cudaFuncSetAttribute(k_label_split<SIL_U8>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+          attr_err = set_resident_attrs(reinterpret_cast<const void*>(k_label_split<SIL_U8>), smem);
       }
     });
     if (attr_err != cudaSuccess) return attr_err;
-    // One CTA of 256 threads per chip: the hardware block scheduler hands
-    // the next chip to whichever slot frees first, which balances chips of
-    // uneven cost (narrow edge chips, chips of one label) better than a
-    // fixed persistent stride (measured 143 vs 162 us on the 10980^2 scene);
-    // 320-thread CTAs were slower at every request size measured (a
-    // 512^2 tile to the 10980^2 scene).
+    // One CTA of 256 threads per chip (grid = the chip count, whatever the
+    // caller's grid): the hardware block scheduler hands the next chip to
+    // whichever slot frees first, which balances chips of uneven cost
+    // (narrow edge chips, chips of one label) better than a fixed
+    // persistent stride (measured 143 vs 162 us on the 10980^2 scene);
+    // 320-thread CTAs were slower at every request size measured (a 512^2
+    // tile to the 10980^2 scene).
     const int64_t nchips = int64_t(r.gx) * r.gy;
+    if (nchips > int64_t(0x7fffffff)) return cudaErrorInvalidConfiguration;
     if constexpr (DT == SIL_U8 && !HS) {
       if (split_all_chips(nchips, slots(smem))) {
         k_label_split<SIL_U8><<<int(nchips * kSplitChip), kThreadsNarrow, smem, s>>>(r, dp, chip, 0);
         return cudaGetLastError();
       }
     }
-    k_label<DT, HS><<<grid, kThreadsNarrow, smem, s>>>(r, dp, chip, nchips);
+    k_label<DT, HS><<<int(nchips), kThreadsNarrow, smem, s>>>(r, dp, chip);
     return cudaGetLastError();
   } else {
     k_label_generic<DT, HS><<<grid, kThreadsNarrow, 0, s>>>(r, dp, chip);

@@ -162,7 +162,7 @@ extern "C" sil_status sil_label_batch_noalloc(const sil_tile* tiles, int32_t n, 
     set_error("sil_label_batch_noalloc: descriptor copy: %s", cudaGetErrorString(e));
     return SIL_ECUDA;
   }
-  const int cps = batch_max_ctas_per_sm(dt, dp.need_hs != 0, chip);
+  const int cps = batch_max_ctas_per_sm(dt, dp.need_hs != 0, chip, kThreadsNarrow);
   const int64_t total = prefix[n];
   const int64_t cap = int64_t(device_sm_count()) * cps;
   const int grid = int(total < cap ? total : cap);

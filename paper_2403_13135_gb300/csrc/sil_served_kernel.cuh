@@ -63,7 +63,7 @@ __device__ __forceinline__ unsigned int ld_acquire32(const unsigned int* p) {
 }
 
 template <int DT, bool HS, bool RESIDENT>
-__global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
+__global__ void __launch_bounds__(kThreadsNarrow, RESIDENT ? ResidentCtas<DT, HS>::k : ((DT == SIL_U8) ? 2 : 1))
     k_served(RingCtl* ctl, const LogEntry* log, int L, SlotDev* slots, unsigned int* complete,
              DevParams dp, int chip, long long ready_ns, long long idle_ns) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -73,6 +73,9 @@ __global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
   __shared__ int s_slot, s_ok, s_got;
   __shared__ unsigned int s_c, s_seq32;
   __shared__ __align__(16) ChipStat st_generic;
+  constexpr uint32_t kCols = PlaneCols<kThreadsNarrow>::kCols;
+  ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
+  if (RESIDENT && !ChipSmem<DT, HS>::kSmemPlane) plane_alloc(&sm.st.tmem, kCols);
   while (true) {
     if (threadIdx.x == 0) {
       // claim a chip: the oldest published request with chips left hands
@@ -178,7 +181,6 @@ __global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
       const Req r = s_req;
       const int64_t cy = s_local / r.gx, cx = s_local - cy * r.gx;
       if (RESIDENT) {
-        ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
         label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, lut);
       } else {
         label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st_generic, lut);
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(kThreadsNarrow, (DT == SIL_U8) ? 2 : 1)
       }
     }
   }
+  if (RESIDENT && !ChipSmem<DT, HS>::kSmemPlane) plane_free(sm.st.tmem, kCols);
 }
 
 // The served kernel's instances of one (dtype, H/S) class.
@@ -228,11 +231,10 @@ template <int DT, bool HS>
 cudaError_t ServedKernels<DT, HS>::prepare(bool resident, size_t smem, int* per_sm) {
   cudaError_t e = cudaSuccess;
   if (resident) {
-    e = cudaFuncSetAttribute(k_served<DT, HS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(smem));
+    e = set_resident_attrs(reinterpret_cast<const void*>(k_served<DT, HS, true>), smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_served<DT, HS, true>,
-                                                        kThreadsNarrow, smem);
+      *per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(k_served<DT, HS, true>),
+                                     kThreadsNarrow, smem, tmem_plane(DT, HS) ? plane_cols(kThreadsNarrow) : 0);
   } else {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_served<DT, HS, false>,
                                                       kThreadsNarrow, 0);

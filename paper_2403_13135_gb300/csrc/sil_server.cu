@@ -48,7 +48,6 @@ namespace sil {
 sil_status check_request(const void* img, int64_t H, int64_t W, int64_t pitch,
                          sil_dtype dt, const uint8_t* labels, int64_t lpitch,
                          const uint64_t* counts);
-size_t resident_smem_bytes(int dt, bool hs);
 int device_sm_count();
 
 }  // namespace sil
