@@ -38,38 +38,39 @@ __global__ void __launch_bounds__(NT, RESIDENT ? ResidentCtas<DT, HS, NT>::k : (
                   int schedule) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   __shared__ uint8_t lut[256];
-  __shared__ long long s_next;
   __shared__ __align__(16) ChipStat st_generic;
-  const int64_t total = prefix[n];
+  __shared__ __align__(16) Req s_req;
+  __shared__ long long s_k, s_cy, s_cx;
   constexpr uint32_t kCols = PlaneCols<NT>::kCols;
   ChipSmem<DT, HS>& sm = *reinterpret_cast<ChipSmem<DT, HS>*>(smem_raw);
   if (RESIDENT && !ChipSmem<DT, HS>::kSmemPlane) plane_alloc(&sm.st.tmem, kCols);
-  int64_t k = blockIdx.x;
-  if (schedule == kSchedQueue) {
-    if (threadIdx.x == 0) s_next = (long long)atomicAdd(head, 1ull);
+  if (threadIdx.x == 0) s_k = schedule == kSchedQueue ? (long long)atomicAdd(head, 1ull) : (long long)blockIdx.x;
+  __syncthreads();
+  while (true) {
+    // the chip's request and position through shared memory, so that no
+    // loop state stays in registers across the chip
+    if (threadIdx.x == 0) {
+      const long long k = s_k;
+      if (k < prefix[n]) {
+        const int t = find_tile(prefix, n, k);
+        s_req = reqs[t];
+        const int64_t local = k - prefix[t];
+        s_cy = local / s_req.gx;
+        s_cx = local - s_cy * s_req.gx;
+      } else {
+        s_cy = -1;
+      }
+    }
     __syncthreads();
-    k = s_next;
-  }
-  while (k < total) {
-    const int t = find_tile(prefix, n, k);
-    const Req& r = reqs[t];
-    const int64_t local = k - prefix[t];
-    const int64_t cy = local / r.gx, cx = local - cy * r.gx;
+    if (s_cy < 0) break;
     if (RESIDENT) {
-      label_chip<DT, HS>(r, dp, chip, cy, cx, sm, lut, lut);  // (batches have no V' output)
+      label_chip<DT, HS>(s_req, dp, chip, s_cy, s_cx, sm, lut, lut);  // (batches have no V' output)
     } else {
-      label_chip_generic<DT, HS>(r, dp, chip, cy, cx, st_generic, lut);
+      label_chip_generic<DT, HS>(s_req, dp, chip, s_cy, s_cx, st_generic, lut);
     }
-    if (schedule == kSchedQueue) {
-      __syncthreads();  // everyone has read s_next
-      if (threadIdx.x == 0) s_next = (long long)atomicAdd(head, 1ull);
-      __syncthreads();
-      k = s_next;
-    } else if (schedule == kSchedStride) {
-      k += gridDim.x;
-    } else {
-      break;
-    }
+    if (schedule == kSchedPerChip) break;
+    __syncthreads();  // every thread is done with s_req and s_k
+    if (threadIdx.x == 0) s_k = schedule == kSchedQueue ? (long long)atomicAdd(head, 1ull) : s_k + gridDim.x;
   }
   if (RESIDENT && !ChipSmem<DT, HS>::kSmemPlane) plane_free(sm.st.tmem, kCols);
 }

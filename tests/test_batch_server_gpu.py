@@ -64,6 +64,12 @@ def test_batch_graph_replay_and_autotune(sil):
     best = sil.autotune(ctx, tiles, len(imgs))
     assert best["schedule"] in (sil.SCHED_STRIDE, sil.SCHED_QUEUE, sil.SCHED_PER_CHIP)
     assert best["threads"] in (256, 320) and best["us"] > 0
+    # the last candidate the tuner ran (fixed-stride persistent CTAs of 320
+    # threads) left its outputs in the buffers: they equal the default's
+    torch.cuda.synchronize()
+    for i in range(len(imgs)):
+        assert np.array_equal(labs[i].cpu().numpy(), a[0][i])
+        assert np.array_equal(cnts[i].cpu().numpy(), a[1][i])
     assert sil.batch_tuning(ctx, tiles, len(imgs)) == (best, True)
     for _ in range(3):  # the same batch replays its cached graph
         sil.label_batch(ctx, tiles, len(imgs))
