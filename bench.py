@@ -284,9 +284,12 @@ def run_sil(args):
     import paper_2403_13135_gb300 as sil
     import synth
 
-    img, _ = synth.full_scene(1 + rank, SIDE)
+    u16 = args.dtype == "u16"
+    img, _ = synth.full_scene(1 + rank, SIDE, dtype=np.uint16 if u16 else np.uint8)
     H, W, _ = img.shape
-    dev = torch.from_numpy(img).cuda()
+    bpp = 6 if u16 else 3  # bytes per input pixel
+    # uint16 images travel as int16 tensors (the same bytes)
+    dev = torch.from_numpy(img.view(np.int16) if u16 else img).cuda()
     lab = torch.empty((H, W), dtype=torch.uint8, device="cuda")
     cnt = torch.empty(4, dtype=torch.int64, device="cuda")
     cc = torch.empty((-(-H // CHIP), -(-W // CHIP), 4), dtype=torch.int32, device="cuda")
@@ -342,7 +345,7 @@ def run_sil(args):
     value = units / el_max / 1e9
 
     # end to end through the host-buffer entry point (pinned host memory)
-    himg = torch.from_numpy(img).pin_memory()
+    himg = torch.from_numpy(img.view(np.uint8).reshape(H, W * bpp)).pin_memory()
     hlab = torch.empty((H, W), dtype=torch.uint8).pin_memory()
     hcnt = np.zeros(4, np.uint64)
     hcc = np.zeros(cc.shape, np.uint32)
@@ -350,7 +353,8 @@ def run_sil(args):
     e2e_steps = max(3, min(args.steps, args.e2e_steps))
 
     def e2e_step():
-        sil.check(sil.sil_label_host(himg.data_ptr(), H, W, 3 * W, sil.SIL_U8, ctypes.byref(p),
+        sil.check(sil.sil_label_host(himg.data_ptr(), H, W, bpp * W, sil.SIL_U16 if u16 else sil.SIL_U8,
+                                     ctypes.byref(p),
                                      hlab.data_ptr(), W, hcnt.ctypes.data, hcc.ctypes.data,
                                      ctypes.c_void_p(stream.cuda_stream)))
 
@@ -370,7 +374,7 @@ def run_sil(args):
     assert np.array_equal(cnt.cpu().numpy().astype(np.uint64), hcnt)
 
     peak, peak_kind = _peaks()
-    alg_bytes = 4.0 * H * W + cc.numel() * 4 + 32
+    alg_bytes = float(bpp + 1) * H * W + cc.numel() * 4 + 32
     avg_launch = float(per_launch.mean())
     achieved = alg_bytes / avg_launch / 1e9
     clocks = sampler.summary()
@@ -384,22 +388,31 @@ def run_sil(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": el_max / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic",
-            "config": {"workload": f"{SIDE}x{SIDE} uint8 RGB scene per GPU, chip {CHIP}, "
-                                   f"labels + per-chip + per-scene counts",
-                       "l2": "input (362 MB) larger than L2, no flush", "parallelism": f"replicas{ws}"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(3 * H * W),
+            "config": {"workload": f"{SIDE}x{SIDE} " + ("uint16 reflectance" if u16 else "uint8")
+                                   + f" RGB scene per GPU, chip {CHIP}, labels + per-chip + per-scene counts",
+                       "l2": f"input ({H * W * bpp / 1e6:.0f} MB) larger than L2, no flush",
+                       "parallelism": f"replicas{ws}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(bpp * H * W),
                     "d2h_bytes_per_step": int(H * W + 32 + cc.numel() * 4)},
             "gpu_launches": int(args.steps),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": args.traffic,
+                         "frac": achieved / peak,
+                         # the committed DRAM figure is the uint8 scene's
+                         "traffic": None if (u16 and args.traffic == TRAFFIC_BYTES_PER_LAUNCH) else args.traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_us": avg_launch * 1e6},
             "clocks": clocks,
         }
-        if not args.no_cpu_baseline and ws == 1:  # rank 0 at N = 1 only
+        if not args.no_cpu_baseline and ws == 1 and u16:
+            # the worker pool shares uint8 scenes; a uint16 scene runs the
+            # oracle on one core only
+            v1, sample1 = cpu_baseline(img, args.cpu_budget)
+            line["cpu_baseline"] = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": sample1}
+        elif not args.no_cpu_baseline and ws == 1:  # rank 0 at N = 1 only
             pool = OraclePool(img, args.cpu_cores or None)
             try:
                 v, sample = pool.run(args.cpu_budget)
@@ -892,6 +905,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cores", type=int, default=0,
                     help="oracle worker processes for the CPU baseline (0 = every host core)")
+    ap.add_argument("--dtype", default="u8", choices=["u8", "u16"],
+                    help="scene workload: uint8 RGB (the headline) or uint16 reflectance")
     ap.add_argument("--config", default="scene",
                     choices=["scene", "batch", "served", "sweep", "unet", "train"],
                     help="scene: the headline line; batch/served/sweep/unet/train: the other workloads")
