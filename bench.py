@@ -178,12 +178,12 @@ def cpu_baseline(img: np.ndarray, budget_s: float = 12.0, seed: int = 0):
 def _chip_worker(task):
     """Pool worker: the oracle on whole chips of the shared scene until the
     budget is spent; returns (pixels, chips)."""
-    name, shape, chips, budget_s = task
+    name, shape, dtype, chips, budget_s = task
     from multiprocessing import shared_memory
     import oracle
     shm = shared_memory.SharedMemory(name=name)
     try:
-        img = np.ndarray(shape, dtype=np.uint8, buffer=shm.buf)
+        img = np.ndarray(shape, dtype=np.dtype(dtype), buffer=shm.buf)
         px, n = 0, 0
         t0 = time.perf_counter()
         for cy, cx in chips:
@@ -215,8 +215,9 @@ class OraclePool:
         from multiprocessing import shared_memory
         self.cores = int(cores or len(os.sched_getaffinity(0)))
         self.shape = img.shape
+        self.dtype = img.dtype.str  # uint8 RGB or uint16 reflectance
         self.shm = shared_memory.SharedMemory(create=True, size=img.nbytes)
-        np.ndarray(img.shape, dtype=np.uint8, buffer=self.shm.buf)[...] = img
+        np.ndarray(img.shape, dtype=img.dtype, buffer=self.shm.buf)[...] = img
         self.pool = mp.get_context("spawn").Pool(self.cores)
         self.pool.map(_worker_ready, range(self.cores), chunksize=1)
 
@@ -224,7 +225,8 @@ class OraclePool:
         gy, gx = -(-self.shape[0] // CHIP), -(-self.shape[1] // CHIP)
         order = np.random.default_rng(seed).permutation(gy * gx)
         chips = [divmod(int(k), gx) for k in order]
-        tasks = [(self.shm.name, self.shape, chips[i::self.cores], budget_s) for i in range(self.cores)]
+        tasks = [(self.shm.name, self.shape, self.dtype, chips[i::self.cores], budget_s)
+                 for i in range(self.cores)]
         t0 = time.perf_counter()
         res = self.pool.map(_chip_worker, tasks, chunksize=1)
         dt = time.perf_counter() - t0
@@ -245,7 +247,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     import synth
-    img, _ = synth.full_scene(1, SIDE)
+    u16 = args.dtype == "u16"
+    img, _ = synth.full_scene(1, SIDE, dtype=np.uint16 if u16 else np.uint8)
     times = []
     sample = ""
     per_step = args.ref_budget / max(1, args.steps + args.warmup)
@@ -262,9 +265,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": (SIDE * SIDE / (value * 1e9) * 1e3) if value else None,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic",
-        "config": {"workload": f"one {SIDE}x{SIDE} uint8 RGB scene, chip {CHIP}, seed 1",
+        "config": {"workload": f"one {SIDE}x{SIDE} " + ("uint16 reflectance" if u16 else "uint8")
+                               + f" RGB scene, chip {CHIP}, seed 1",
                    "l2": "input larger than L2"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                          "sample": f"per step: {sample}"},
@@ -406,13 +410,7 @@ def run_sil(args):
                          "avg_launch_us": avg_launch * 1e6},
             "clocks": clocks,
         }
-        if not args.no_cpu_baseline and ws == 1 and u16:
-            # the worker pool shares uint8 scenes; a uint16 scene runs the
-            # oracle on one core only
-            v1, sample1 = cpu_baseline(img, args.cpu_budget)
-            line["cpu_baseline"] = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": sample1}
-        elif not args.no_cpu_baseline and ws == 1:  # rank 0 at N = 1 only
+        if not args.no_cpu_baseline and ws == 1:  # rank 0 at N = 1 only
             pool = OraclePool(img, args.cpu_cores or None)
             try:
                 v, sample = pool.run(args.cpu_budget)
