@@ -39,3 +39,14 @@ def test_reference_arm_other_ranks_exit_quietly():
     lines = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--steps", "1", "--warmup", "0",
                  "--gpus", "2")
     assert lines == []
+
+
+def test_reference_arm_uint16_scene():
+    """--dtype u16: the oracle pool shares the uint16 reflectance scene."""
+    lines = _run(None, "--dtype", "u16", "--steps", "1", "--warmup", "0", "--ref-budget", "2",
+                 "--cpu-cores", "2")
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["dtype"] == "u16" and d["value"] > 0
+    assert "uint16" in d["config"]["workload"]
+    assert d["cpu_baseline"]["cores"] == 2 and d["cpu_baseline"]["value"] == d["value"]
